@@ -1,0 +1,177 @@
+"""ctypes front end of the FP64 CPU oracle (``boxspline_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: only tests/, ``__graft_entry__.smoke()`` and the CPU-baseline /
+reference leg of ``bench.py`` may import this module.  The CUDA product path never imports,
+links or runs anything under ``oracle/``; the two share no code.
+
+What it computes (Horacsek & Alim, arXiv 2102.08514):
+
+* ``Spline.M``      -- the box spline M_Xi of Sec. 3 (base case 1/|det Xi| on Xi[0,1)^s, support the
+  zonotope), by de Boor's recurrence with exact decisions (see the C file's header).
+* ``Spline.phi``    -- the centred, normalised basis phi(x) = |det L| M_Xi(x + sum(Xi)/2), so that
+  phi has partition of unity on L Z^s (Sec. 4.1 requires it).
+* ``eval_sum``      -- the convolution sum of Eq. 1 (h = 1) split over the Cartesian cosets of
+  Sec. 4.1, f(x) = sum_k sum_i c_k[i] phi(x - D i - l_k), summed by brute force; optional grad.
+* ``adjoint``       -- dL/dc_k[i] = sum_q g_q phi(x_q - D i - l_k).
+* ``cells``         -- the exact shift rho to the region of evaluation (Sec. 4.1), here the cube
+  [-D/2, D/2)^s centred on the nearest site of each coset.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from itertools import product
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "boxspline_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle into oracle/_build/liboracle.so (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu11",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        I64 = ctypes.c_int64
+        lib.orc_create.argtypes = [ctypes.c_int, ctypes.c_int, P, ctypes.c_double, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_void_p)]
+        lib.orc_destroy.argtypes = [P]
+        lib.orc_M.argtypes = [P, ctypes.c_uint, I64, P, P]
+        lib.orc_phi.argtypes = [P, I64, P, P, P]
+        lib.orc_eval.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P, I64, P, P, P, ctypes.c_int]
+        lib.orc_adjoint.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, I64, P, P, P]
+        lib.orc_cells.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, I64, P, P, P]
+        for f in (lib.orc_create, lib.orc_M, lib.orc_phi, lib.orc_eval, lib.orc_adjoint, lib.orc_cells):
+            f.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with code {rc}"
+                           + (" (point not exactly representable)" if rc == 2 else ""))
+
+
+class Spline:
+    """A box spline M_Xi (columns of ``xi`` are the directions) and its centred basis phi.
+
+    ``det_l`` is |det L| of the lattice phi is used on; ``tmode`` picks the solution t of Xi t = x
+    used by the recurrence (0: minimum norm, 1: supported on a basis) -- both are valid, which is
+    what the two-t agreement test checks.
+    """
+
+    def __init__(self, xi, det_l: float = 1.0, tmode: int = 0):
+        xi = np.asarray(xi, dtype=np.int64)
+        if xi.ndim != 2:
+            raise ValueError("xi must be an s x n integer matrix")
+        self.xi = xi
+        self.s, self.n = xi.shape
+        self.det_l = float(det_l)
+        cols = np.ascontiguousarray(xi.T, dtype=np.int32)
+        h = ctypes.c_void_p()
+        _check(_load().orc_create(self.s, self.n, _ptr(cols), self.det_l, tmode, ctypes.byref(h)),
+               "create")
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.orc_destroy(self._h)
+            self._h = None
+
+    @property
+    def halfwidth(self) -> np.ndarray:
+        return np.abs(self.xi).sum(axis=1) / 2.0
+
+    def M(self, w, mask: int | None = None) -> np.ndarray:
+        """Raw M_{Xi_mask}(w) (uncentred, integral 1); mask defaults to all columns."""
+        w = np.ascontiguousarray(np.atleast_2d(np.asarray(w, dtype=np.float64)))
+        out = np.empty(w.shape[0])
+        m = (1 << self.n) - 1 if mask is None else mask
+        _check(_load().orc_M(self._h, m, w.shape[0], _ptr(w), _ptr(out)), "M")
+        return out
+
+    def phi(self, z, grad: bool = False):
+        z = np.ascontiguousarray(np.atleast_2d(np.asarray(z, dtype=np.float64)))
+        out = np.empty(z.shape[0])
+        g = np.empty_like(z) if grad else None
+        _check(_load().orc_phi(self._h, z.shape[0], _ptr(z), _ptr(out), _ptr(g)), "phi")
+        return (out, g) if grad else out
+
+
+def lattice_sites(L, lo, hi) -> np.ndarray:
+    """All points of L Z^s inside the box [lo, hi] (integer L), by a membership test on Z^s:
+    z is a site iff adj(L) z = 0 mod det L.  Independent of any coset decomposition."""
+    L = np.asarray(L, dtype=np.int64)
+    s = L.shape[0]
+    det = int(round(np.linalg.det(L)))
+    adj = np.round(np.linalg.inv(L) * det).astype(np.int64)
+    rng = [range(int(np.ceil(lo[a])), int(np.floor(hi[a])) + 1) for a in range(s)]
+    pts = np.array(list(product(*rng)), dtype=np.int64).reshape(-1, s)
+    keep = np.all((pts @ adj.T) % abs(det) == 0, axis=1)
+    return pts[keep]
+
+
+def eval_sum(spline: Spline, D: int, cosets, coeffs, points, grad: bool = False, nthreads: int = 0):
+    """f(x_q) = sum_k sum_i c_k[i] phi(x_q - D i - l_k) (and grad f) in FP64, brute force.
+
+    ``coeffs`` has shape (M, N_1, ..., N_s) (coset-major, last axis fastest); points (Q, s).
+    Outside the stored arrays the coefficients are taken as 0.
+    """
+    c = np.ascontiguousarray(coeffs, dtype=np.float64)
+    lk = np.ascontiguousarray(cosets, dtype=np.int32).reshape(-1, spline.s)
+    dims = np.ascontiguousarray(c.shape[1:], dtype=np.int32)
+    p = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, spline.s)
+    out = np.empty(p.shape[0])
+    g = np.empty_like(p) if grad else None
+    _check(_load().orc_eval(spline._h, D, lk.shape[0], _ptr(lk), _ptr(dims), _ptr(c), p.shape[0],
+                            _ptr(p), _ptr(out), _ptr(g), nthreads), "eval")
+    return (out, g) if grad else out
+
+
+def adjoint(spline: Spline, D: int, cosets, shape, points, g) -> np.ndarray:
+    """dL/dc for dL/df = g: sum_q g_q phi(x_q - D i - l_k), in the coefficient layout ``shape``."""
+    lk = np.ascontiguousarray(cosets, dtype=np.int32).reshape(-1, spline.s)
+    dims = np.ascontiguousarray(shape[1:], dtype=np.int32)
+    p = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, spline.s)
+    gg = np.ascontiguousarray(g, dtype=np.float64)
+    d = np.zeros(shape, dtype=np.float64)
+    _check(_load().orc_adjoint(spline._h, D, lk.shape[0], _ptr(lk), _ptr(dims), p.shape[0], _ptr(p),
+                               _ptr(gg), _ptr(d)), "adjoint")
+    return d
+
+
+def cells(s: int, D: int, cosets, points):
+    """Exact nearest coset site i (Q, M, s) int32 and offset y = x - l_k - D i (Q, M, s)."""
+    lk = np.ascontiguousarray(cosets, dtype=np.int32).reshape(-1, s)
+    p = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, s)
+    q, m = p.shape[0], lk.shape[0]
+    ci = np.empty((q, m, s), dtype=np.int32)
+    off = np.empty((q, m, s), dtype=np.float64)
+    _check(_load().orc_cells(s, D, m, _ptr(lk), q, _ptr(p), _ptr(ci), _ptr(off)), "cells")
+    return ci, off
+
+
+def folded_offsets(offsets: np.ndarray) -> np.ndarray:
+    """Fold offsets into the chamber D/2 >= y_1 >= ... >= y_s >= 0 of the signed permutations
+    (the reflection of Sec. 4.2 generalised to the full symmetry group of the cube)."""
+    return -np.sort(-np.abs(offsets), axis=-1)
