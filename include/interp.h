@@ -1,0 +1,148 @@
+/*
+ * interp.h -- C ABI of the B300 (sm_103a) lattice convolution-sum evaluator.
+ *
+ * Operation (Horacsek & Alim, arXiv 2102.08514, Eq. 1 with h = 1, split over Cartesian cosets as
+ * in Sec. 4.1):
+ *
+ *     f(x) = sum_k sum_i c_k[i] * phi(x - (D i + l_k)),      phi(x) = |det L| * M_Xi(x + sum(Xi)/2)
+ *
+ * where M_Xi is the box spline of Sec. 3 with direction matrix Xi, L Z^s = U_k (D Z^s + l_k) is
+ * the lattice, and c_k is the coefficient array of coset k.  phi is centred at the origin and
+ * scaled so that it has partition of unity on L Z^s.  Coordinates are in the paper's integer
+ * frame: BCC = {all coordinates of equal parity}, FCC = {even coordinate sum}, D4* = {all four
+ * coordinates of equal parity}; D = 2 for those three, D = 1 for the Cartesian lattice.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an interp_status and never aborts or prints.
+ *   - Points are FP32, row-major (npts x s).  Outputs are FP32.
+ *   - Point, output and gradient buffers are DEVICE pointers owned by the caller; the library
+ *     keeps no pointer to them after the call returns.  Calls are asynchronous on `stream`
+ *     (a cudaStream_t passed as void*; NULL = the legacy default stream).
+ *   - Coefficients outside the stored arrays are zero ("zero extension"): a query far outside
+ *     the data returns 0.  A query with a NaN or infinite coordinate returns NaN.
+ *   - A handle may be used from several streams at once for eval calls (read-only).  Calls that
+ *     write the handle's coefficients (interp_set_coeffs) or its internal gradient buffer
+ *     (interp_backward) must not overlap other calls on the same handle.
+ */
+#ifndef INTERP_B300_H
+#define INTERP_B300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct interp interp_t; /* opaque; owns the halo-padded coefficient arrays */
+
+typedef enum {
+    INTERP_OK = 0,
+    INTERP_EINVAL = 1,       /* bad argument: null pointer, negative size, singular L, ...      */
+    INTERP_EUNSUPPORTED = 2, /* (L, Xi) has no generated tables in this build, or s not in 3..4 */
+    INTERP_ENOMEM = 3,       /* device or host allocation failed                                */
+    INTERP_ECUDA = 4,        /* a CUDA runtime call or kernel launch failed                     */
+    INTERP_ESIZE = 5         /* a size exceeds a documented limit                               */
+} interp_status;
+
+typedef enum {
+    INTERP_F32 = 0,
+    INTERP_F16 = 1,   /* IEEE binary16 storage, FP32 arithmetic */
+    INTERP_BF16 = 2,  /* bfloat16 storage, FP32 arithmetic      */
+    INTERP_F64 = 3    /* accepted as a SOURCE type by interp_set_coeffs only (rounded to storage) */
+} interp_dtype;
+
+/* Human-readable text of a status code (static storage). */
+const char *interp_strerror(interp_status st);
+
+/* Built-in splines: the (L, Xi) pairs whose generated tables are compiled into this library.
+ * interp_num_splines() returns their count; interp_spline_name(i) their names (NULL if out of
+ * range); interp_table_digest() the digest of the generated tables. */
+int interp_num_splines(void);
+const char *interp_spline_name(int i);
+const char *interp_table_digest(void);
+
+/*
+ * interp_create -- build a handle for the lattice L Z^s (L: s x s integer, row-major, full rank)
+ * and the box spline with direction matrix Xi (s x n integer, row-major; column order and column
+ * signs do not matter, the spline is centred).  dims[a] is the number of samples per axis of
+ * EVERY coset array (array k holds the sites D i + l_k, 0 <= i_a < dims[a]).
+ *
+ * storage selects the device storage type of the coefficients (F32, F16 or BF16).  The handle
+ * allocates the coefficient arrays with a zero halo of 2*HALO sites per side (HALO = the largest
+ * stencil offset of the spline), so gathers need no bounds checks.  Coefficients start at zero;
+ * set them with interp_set_coeffs.
+ *
+ * Errors: EINVAL (null pointers, dims < 1, singular L, L^{-1} Xi not integer), EUNSUPPORTED (no
+ * generated tables for this (L, Xi)), ESIZE (padded arrays above 2^31 - 1 elements), ENOMEM,
+ * ECUDA.  On error *out is set to NULL.
+ */
+interp_status interp_create(int s, const int32_t *L, const int32_t *xi, int n, const int32_t *dims,
+                            interp_dtype storage, interp_t **out);
+
+/* Release the handle and its device memory (NULL is a no-op). Synchronises the device. */
+void interp_destroy(interp_t *h);
+
+/* Shape queries: spline dimension s, coset count M, coset spacing D, table name. */
+typedef struct {
+    int s, n_cosets, D, halo, n_pieces, degree, n_monomials;
+    int dims[4];
+    int32_t cosets[8][4];
+    double lookups_per_query;     /* expected coefficient reads per query (all cosets)      */
+    double fma_value_per_query;   /* FP32 FMAs of one value evaluation (A c + Horner)       */
+    double fma_grad_per_query;    /* FP32 FMAs of one value + gradient evaluation           */
+    int64_t coeff_count;          /* n_cosets * prod(dims)                                  */
+    const char *name;
+} interp_info_t;
+interp_status interp_info(const interp_t *h, interp_info_t *info);
+
+/*
+ * interp_set_coeffs -- copy the coefficients into the handle, converting to the storage type.
+ * src: n_cosets * prod(dims) values of type src_dtype (F32, F16, BF16 or F64), coset-major, then
+ * row-major with the last axis fastest.  src_on_device = 1 for a device pointer, 0 for a host
+ * pointer (host data is staged through pageable memcpy; the call then blocks until the copy is
+ * done).  Stream-ordered on `stream`.  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+interp_status interp_set_coeffs(interp_t *h, const void *src, interp_dtype src_dtype, int src_on_device,
+                                void *stream);
+
+/*
+ * interp_eval -- out[q] = f(pts[q]) for q < npts (Sec. 4, Algorithm 1, per query: coset loop,
+ * shift to the region of evaluation, symmetry fold, branch-free piece selection by plane sign
+ * bits, coefficient gather, Horner evaluation in FP32 FMA).  npts = 0 is a no-op.
+ */
+interp_status interp_eval(const interp_t *h, const float *pts, int64_t npts, float *out, void *stream);
+
+/*
+ * interp_eval_grad -- out[q] = f(pts[q]) and grad[q*s + a] = d f / d x_a at pts[q], from the
+ * analytic derivatives of the piece polynomials (not in the paper; same path as interp_eval).
+ * out may be NULL when only the gradient is wanted.
+ */
+interp_status interp_eval_grad(const interp_t *h, const float *pts, int64_t npts, float *out, float *grad,
+                               void *stream);
+
+/*
+ * interp_backward -- adjoint of interp_eval (not in the paper).  Given gout[q] = dLoss/df(pts[q]):
+ *     dcoeffs[k][i] += sum_q gout[q] * phi(pts[q] - D i - l_k)      (FP32, caller's layout, +=)
+ *     dpts[q*s + a]  = gout[q] * d f / d x_a (pts[q])               (if dpts != NULL)
+ * dcoeffs has the coefficient layout of interp_set_coeffs (FP32) and is ACCUMULATED into: zero it
+ * first for a plain gradient.  The scatter uses FP32 atomics into a handle-owned padded buffer,
+ * so the order of additions, and the last bits of dcoeffs, vary between runs.  dcoeffs may be
+ * NULL to compute dpts only.
+ */
+interp_status interp_backward(interp_t *h, const float *pts, int64_t npts, const float *gout, float *dcoeffs,
+                              float *dpts, void *stream);
+
+/*
+ * interp_debug_indices -- for every query q and coset k: cells[(q*M + k)*s + a] = the index i of
+ * the nearest coset site (the exact shift rho of Sec. 4.1 to the cube [-D/2, D/2)^s), and
+ * piece[q*M + k] = the sub-region index j (Sec. 4.2) of the folded offset.  Either pointer may
+ * be NULL.
+ */
+interp_status interp_debug_indices(const interp_t *h, const float *pts, int64_t npts, int32_t *cells,
+                                   int32_t *piece, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* INTERP_B300_H */

@@ -19,6 +19,7 @@ What it computes (Horacsek & Alim, arXiv 2102.08514):
 from __future__ import annotations
 
 import ctypes
+import hashlib
 import os
 import subprocess
 from itertools import product
@@ -32,13 +33,20 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile the C oracle into oracle/_build/liboracle.so (gcc, OpenMP)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile the C oracle into oracle/_build/liboracle.so (gcc, OpenMP); rebuilt when the
+    source's hash differs from the one recorded beside the library."""
+    with open(_SRC, "rb") as f:
+        digest = hashlib.sha256(f.read()).hexdigest()
+    stamp = _LIB + ".stamp"
+    current = os.path.exists(_LIB) and os.path.exists(stamp) and open(stamp).read().strip() == digest
+    if force or not current:
         os.makedirs(os.path.dirname(_LIB), exist_ok=True)
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu11",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
+        with open(stamp, "w") as f:
+            f.write(digest)
     return _LIB
 
 

@@ -1,0 +1,293 @@
+"""Thin ctypes binding of the C ABI in include/interp.h (argument marshalling only).
+
+Every computation runs in the CUDA kernels of libinterp_b300.so; this module only converts torch
+tensors to device pointers and the current CUDA stream to a cudaStream_t.  If the library is
+missing, loading fails loudly: there is no CPU or PyTorch fallback.
+
+The functions carry the C names (interp_create, interp_eval, ...); ``Interpolator`` bundles a
+handle with its tensors and ``LatticeInterp`` is the torch.autograd.Function whose backward is the
+hand-written adjoint (interp_backward).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libinterp_b300.so")
+
+INTERP_OK, INTERP_EINVAL, INTERP_EUNSUPPORTED, INTERP_ENOMEM, INTERP_ECUDA, INTERP_ESIZE = range(6)
+INTERP_F32, INTERP_F16, INTERP_BF16, INTERP_F64 = range(4)
+
+_lib = None
+
+
+class InterpError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {_strerror(status)} (status {status})")
+
+
+class InterpInfo(ctypes.Structure):
+    _fields_ = [("s", ctypes.c_int), ("n_cosets", ctypes.c_int), ("D", ctypes.c_int), ("halo", ctypes.c_int),
+                ("n_pieces", ctypes.c_int), ("degree", ctypes.c_int), ("n_monomials", ctypes.c_int),
+                ("dims", ctypes.c_int * 4), ("cosets", (ctypes.c_int32 * 4) * 8),
+                ("lookups_per_query", ctypes.c_double), ("fma_value_per_query", ctypes.c_double),
+                ("fma_grad_per_query", ctypes.c_double), ("coeff_count", ctypes.c_int64),
+                ("name", ctypes.c_char_p)]
+
+
+def load(path: str = LIB_PATH):
+    """Load libinterp_b300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run python -m paper_2102_08514_b300.build)")
+    lib = ctypes.CDLL(path)
+    P, I64, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    lib.interp_strerror.argtypes = [I]
+    lib.interp_strerror.restype = ctypes.c_char_p
+    lib.interp_num_splines.restype = I
+    lib.interp_spline_name.argtypes = [I]
+    lib.interp_spline_name.restype = ctypes.c_char_p
+    lib.interp_table_digest.restype = ctypes.c_char_p
+    lib.interp_create.argtypes = [I, P, P, I, P, I, ctypes.POINTER(ctypes.c_void_p)]
+    lib.interp_destroy.argtypes = [P]
+    lib.interp_destroy.restype = None
+    lib.interp_info.argtypes = [P, ctypes.POINTER(InterpInfo)]
+    lib.interp_set_coeffs.argtypes = [P, P, I, I, P]
+    lib.interp_eval.argtypes = [P, P, I64, P, P]
+    lib.interp_eval_grad.argtypes = [P, P, I64, P, P, P]
+    lib.interp_backward.argtypes = [P, P, I64, P, P, P, P]
+    lib.interp_debug_indices.argtypes = [P, P, I64, P, P, P]
+    for f in (lib.interp_create, lib.interp_info, lib.interp_set_coeffs, lib.interp_eval, lib.interp_eval_grad,
+              lib.interp_backward, lib.interp_debug_indices):
+        f.restype = I
+    _lib = lib
+    return lib
+
+
+def exported_symbols() -> list[str]:
+    return ["interp_strerror", "interp_num_splines", "interp_spline_name", "interp_table_digest",
+            "interp_create", "interp_destroy", "interp_info", "interp_set_coeffs", "interp_eval",
+            "interp_eval_grad", "interp_backward", "interp_debug_indices"]
+
+
+def _strerror(st: int) -> str:
+    try:
+        return load().interp_strerror(st).decode()
+    except Exception:  # library not loadable
+        return "error"
+
+
+def _check(st: int, what: str):
+    if st != INTERP_OK:
+        raise InterpError(st, what)
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t, name, dtype=None, device=True):
+    if t is None:
+        return None
+    import torch
+    if device and not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def spline_names() -> list[str]:
+    lib = load()
+    return [lib.interp_spline_name(i).decode() for i in range(lib.interp_num_splines())]
+
+
+def table_digest() -> str:
+    return load().interp_table_digest().decode()
+
+
+# ----------------------------------------------------------------------------- C-named wrappers
+
+def interp_create(L, xi, dims, storage: int = INTERP_F32):
+    """Create a handle for lattice L (s x s) and direction matrix xi (s x n); dims = samples per
+    axis of every coset array.  Returns an opaque ctypes pointer."""
+    L = np.ascontiguousarray(L, dtype=np.int32)
+    xi = np.ascontiguousarray(xi, dtype=np.int32)
+    dims = np.ascontiguousarray(dims, dtype=np.int32)
+    s = L.shape[0]
+    h = ctypes.c_void_p()
+    _check(load().interp_create(s, L.ctypes.data, xi.ctypes.data, xi.shape[1], dims.ctypes.data, storage,
+                                ctypes.byref(h)), "interp_create")
+    return h
+
+
+def interp_destroy(h):
+    if h:
+        load().interp_destroy(h)
+
+
+def interp_info(h) -> InterpInfo:
+    info = InterpInfo()
+    _check(load().interp_info(h, ctypes.byref(info)), "interp_info")
+    return info
+
+
+def interp_set_coeffs(h, coeffs, stream=None):
+    """coeffs: torch tensor (CUDA or CPU) of float32/float64/float16/bfloat16 in the coset-major
+    layout (n_cosets, *dims)."""
+    import torch
+    dt = {torch.float32: INTERP_F32, torch.float16: INTERP_F16, torch.bfloat16: INTERP_BF16,
+          torch.float64: INTERP_F64}[coeffs.dtype]
+    c = coeffs.contiguous()
+    _check(load().interp_set_coeffs(h, ctypes.c_void_p(c.data_ptr()), dt, int(c.is_cuda),
+                                    _stream(stream) if c.is_cuda else _stream(stream)), "interp_set_coeffs")
+
+
+def interp_eval(h, pts, out, stream=None):
+    import torch
+    _check(load().interp_eval(h, _dptr(pts, "pts", torch.float32), pts.shape[0], _dptr(out, "out", torch.float32),
+                              _stream(stream)), "interp_eval")
+
+
+def interp_eval_grad(h, pts, out, grad, stream=None):
+    import torch
+    _check(load().interp_eval_grad(h, _dptr(pts, "pts", torch.float32), pts.shape[0],
+                                   _dptr(out, "out", torch.float32), _dptr(grad, "grad", torch.float32),
+                                   _stream(stream)), "interp_eval_grad")
+
+
+def interp_backward(h, pts, gout, dcoeffs, dpts=None, stream=None):
+    import torch
+    _check(load().interp_backward(h, _dptr(pts, "pts", torch.float32), pts.shape[0],
+                                  _dptr(gout, "gout", torch.float32), _dptr(dcoeffs, "dcoeffs", torch.float32),
+                                  _dptr(dpts, "dpts", torch.float32), _stream(stream)), "interp_backward")
+
+
+def interp_debug_indices(h, pts, cells=None, piece=None, stream=None):
+    import torch
+    _check(load().interp_debug_indices(h, _dptr(pts, "pts", torch.float32), pts.shape[0],
+                                       _dptr(cells, "cells", torch.int32), _dptr(piece, "piece", torch.int32),
+                                       _stream(stream)), "interp_debug_indices")
+
+
+# ----------------------------------------------------------------------------- convenience object
+
+STORAGE = {"f32": INTERP_F32, "f16": INTERP_F16, "bf16": INTERP_BF16}
+
+
+class Interpolator:
+    """A handle plus its shape: f(x) = sum_k sum_i c_k[i] phi(x - D i - l_k) on one device."""
+
+    def __init__(self, L, xi, dims, storage: str = "f32", coeffs=None):
+        self.L = np.asarray(L, dtype=np.int32)
+        self.xi = np.asarray(xi, dtype=np.int32)
+        self.dims = tuple(int(d) for d in dims)
+        self.storage = storage
+        self._h = interp_create(self.L, self.xi, self.dims, STORAGE[storage])
+        self.info = interp_info(self._h)
+        self.s = self.info.s
+        self.n_cosets = self.info.n_cosets
+        self.shape = (self.n_cosets,) + self.dims
+        if coeffs is not None:
+            self.set_coeffs(coeffs)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            interp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_coeffs(self, coeffs, stream=None):
+        if tuple(coeffs.shape) != self.shape:
+            raise ValueError(f"coefficients must have shape {self.shape}, got {tuple(coeffs.shape)}")
+        interp_set_coeffs(self._h, coeffs, stream)
+
+    def eval(self, pts, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(pts.shape[0], device=pts.device, dtype=torch.float32)
+        interp_eval(self._h, pts, out, stream)
+        return out
+
+    def eval_grad(self, pts, out=None, grad=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(pts.shape[0], device=pts.device, dtype=torch.float32)
+        if grad is None:
+            grad = torch.empty(pts.shape[0], self.s, device=pts.device, dtype=torch.float32)
+        interp_eval_grad(self._h, pts, out, grad, stream)
+        return out, grad
+
+    def backward(self, pts, gout, dcoeffs=None, want_dpts=False, stream=None):
+        import torch
+        if dcoeffs is None:
+            dcoeffs = torch.zeros(self.shape, device=pts.device, dtype=torch.float32)
+        dpts = torch.empty(pts.shape[0], self.s, device=pts.device, dtype=torch.float32) if want_dpts else None
+        interp_backward(self._h, pts, gout, dcoeffs, dpts, stream)
+        return dcoeffs, dpts
+
+    def debug_indices(self, pts, stream=None):
+        import torch
+        cells = torch.empty(pts.shape[0], self.n_cosets, self.s, device=pts.device, dtype=torch.int32)
+        piece = torch.empty(pts.shape[0], self.n_cosets, device=pts.device, dtype=torch.int32)
+        interp_debug_indices(self._h, pts, cells, piece, stream)
+        return cells, piece
+
+
+def _autograd_function():
+    import torch
+
+    class LatticeInterp(torch.autograd.Function):
+        """f = LatticeInterp.apply(pts, coeffs, interpolator): forward runs interp_eval with the
+        handle's coefficients set from `coeffs`; backward runs the hand-written adjoint
+        (dL/dcoeffs by the scatter kernel, dL/dpts = g * grad f)."""
+
+        @staticmethod
+        def forward(ctx, pts, coeffs, interp: Interpolator):
+            interp.set_coeffs(coeffs.detach())
+            ctx.interp = interp
+            ctx.save_for_backward(pts)
+            return interp.eval(pts.detach().contiguous())
+
+        @staticmethod
+        def backward(ctx, g):
+            (pts,) = ctx.saved_tensors
+            interp = ctx.interp
+            want_c = ctx.needs_input_grad[1]
+            want_x = ctx.needs_input_grad[0]
+            dc = torch.zeros(interp.shape, device=pts.device, dtype=torch.float32) if want_c else None
+            dx = torch.empty(pts.shape[0], interp.s, device=pts.device, dtype=torch.float32) if want_x else None
+            interp_backward(interp.handle, pts.detach().contiguous(), g.contiguous().float(), dc, dx)
+            return dx, dc, None
+
+    return LatticeInterp
+
+
+_LatticeInterp = None
+
+
+def lattice_interp(pts, coeffs, interp: Interpolator):
+    """Differentiable f(pts) w.r.t. pts and coeffs (autograd through the hand-written adjoint)."""
+    global _LatticeInterp
+    if _LatticeInterp is None:
+        _LatticeInterp = _autograd_function()
+    return _LatticeInterp.apply(pts, coeffs, interp)

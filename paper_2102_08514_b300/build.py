@@ -1,0 +1,115 @@
+"""Build the CUDA library in-tree:  python -m paper_2102_08514_b300.build [--force] [--ptxas-v]
+
+Compiles for sm_103a only.  The ABI (csrc/interp.cu) and one instantiation unit per (spline,
+kernel family) (csrc/ops_inst.cu with -DINTERP_SPLINE / -DINTERP_PART) compile in parallel into
+paper_2102_08514_b300/_build/obj/, then link into _build/libinterp_b300.so.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import hashlib
+import os
+import re
+import shutil
+import subprocess
+import sys
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+CSRC = os.path.join(PKG, "csrc")
+BUILD = os.path.join(PKG, "_build")
+OUT = os.path.join(BUILD, "libinterp_b300.so")
+GEN_HDR = os.path.join(CSRC, "generated", "splines.h")
+COMMON_DEPS = [os.path.join(CSRC, f) for f in ("kernels.cuh", "registry.h", "ops_inst.cu", "interp.cu")] + \
+    [GEN_HDR, os.path.join(ROOT, "include", "interp.h")]
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ["-O3", "-std=c++20", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+              "-Xptxas", "-O3"]
+N_PARTS = 4
+
+
+def nvcc() -> str:
+    for cand in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found")
+
+
+def spline_names() -> list[str]:
+    text = open(GEN_HDR).read()
+    m = re.search(r"#define INTERP_GEN_SPLINES\(X\) (.*)", text)
+    return re.findall(r"X\((\w+)\)", m.group(1))
+
+
+STAMP = os.path.join(BUILD, "libinterp_b300.stamp")
+
+
+def source_digest() -> str:
+    """Hash of every source, header and flag the library depends on (file times need not survive
+    a copy of the tree, contents do)."""
+    h = hashlib.sha256(" ".join(NVCC_FLAGS).encode())
+    for p in sorted(COMMON_DEPS):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def needs_build() -> bool:
+    if not os.path.exists(OUT) or not os.path.exists(STAMP):
+        return True
+    with open(STAMP) as f:
+        return f.read().strip() != source_digest()
+
+
+def _compile(args):
+    cmd, log = args
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    return cmd, r.returncode, r.stdout + r.stderr
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False, jobs: int | None = None) -> str:
+    if not force and not needs_build():
+        return OUT
+    objdir = os.path.join(BUILD, "obj")
+    os.makedirs(objdir, exist_ok=True)
+    inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
+    extra = ["-Xptxas", "-v"] if ptxas_v else []
+    jobsl = []
+    objs = []
+    o = os.path.join(objdir, "interp.o")
+    jobsl.append(([nvcc(), *NVCC_FLAGS, *inc, "-c", os.path.join(CSRC, "interp.cu"), "-o", o], None))
+    objs.append(o)
+    for name in spline_names():
+        for part in range(N_PARTS):
+            o = os.path.join(objdir, f"ops_{name}_{part}.o")
+            jobsl.append(([nvcc(), *NVCC_FLAGS, *extra, *inc, f"-DINTERP_SPLINE={name}", f"-DINTERP_PART={part}",
+                           "-c", os.path.join(CSRC, "ops_inst.cu"), "-o", o], None))
+            objs.append(o)
+    # the 4-D spline's units need several GB each: at most two of them run at a time
+    big = [j for j in jobsl if "d4s" in " ".join(j[0])]
+    small = [j for j in jobsl if "d4s" not in " ".join(j[0])]
+    logs = []
+    with cf.ThreadPoolExecutor(max_workers=2) as exb, \
+            cf.ThreadPoolExecutor(max_workers=max(1, (jobs or os.cpu_count() or 4) - 2)) as exs:
+        futs = [exb.submit(_compile, j) for j in big] + [exs.submit(_compile, j) for j in small]
+        for fu in futs:
+            cmd, rc, out = fu.result()
+            if verbose or rc != 0:
+                logs.append(" ".join(cmd) + "\n" + out)
+            if rc != 0:
+                sys.stderr.write("\n".join(logs))
+                raise RuntimeError(f"nvcc failed: {' '.join(cmd)}")
+    if verbose:
+        sys.stderr.write("\n".join(logs))
+    tmp = OUT + f".tmp{os.getpid()}"
+    subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
+    os.replace(tmp, OUT)
+    with open(STAMP, "w") as f:
+        f.write(source_digest())
+    return OUT
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv or "--ptxas-v" in sys.argv,
+                ptxas_v="--ptxas-v" in sys.argv))

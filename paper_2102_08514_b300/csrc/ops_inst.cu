@@ -1,0 +1,93 @@
+// ops_inst.cu -- instantiates the kernels of ONE spline and ONE kernel family.  The build
+// compiles this file once per (spline, family) with -DINTERP_SPLINE=<name> -DINTERP_PART=<0..3>
+// so the large unrolled kernels compile in parallel.
+#include "kernels.cuh"
+#include "registry.h"
+
+#ifndef INTERP_SPLINE
+#error "compile with -DINTERP_SPLINE=<spline struct name>"
+#endif
+#ifndef INTERP_PART
+#error "compile with -DINTERP_PART=<0..3>"
+#endif
+
+#define IB_CAT2(a, b, c, d) a##b##c##d
+#define IB_CAT(a, b, c, d) IB_CAT2(a, b, c, d)
+
+namespace {
+
+constexpr int kTPB = 128;
+using SP = interp_gen::INTERP_SPLINE;
+
+template <class CT>
+ib::DevVol<CT> make_vol(const void *c, const int *n, const int *stride, int coset_elems)
+{
+    ib::DevVol<CT> v;
+    v.c = static_cast<const CT *>(c);
+    for (int a = 0; a < 4; ++a) {
+        v.n[a] = n[a];
+        v.stride[a] = stride[a];
+    }
+    v.coset_elems = coset_elems;
+    return v;
+}
+
+inline unsigned grid_for(int64_t n) { return (unsigned)((n + kTPB - 1) / kTPB); }
+
+template <class CT, int MODE>
+cudaError_t launch_eval(const float *pts, int64_t n, const void *c, const int *dims, const int *stride, int ce,
+                        float *out, float *grad, const float *gout, cudaStream_t st)
+{
+    ib::k_eval<SP, CT, MODE><<<grid_for(n), kTPB, 0, st>>>(pts, n, make_vol<CT>(c, dims, stride, ce), out, grad, gout);
+    return cudaPeekAtLastError();
+}
+
+[[maybe_unused]] cudaError_t launch_adjoint(const float *pts, int64_t n, const float *gout, const int *dims,
+                                            const int *stride, int ce, float *dpad, cudaStream_t st)
+{
+    ib::k_adjoint<SP><<<grid_for(n), kTPB, 0, st>>>(pts, n, gout, make_vol<float>(nullptr, dims, stride, ce), dpad);
+    return cudaPeekAtLastError();
+}
+
+[[maybe_unused]] cudaError_t launch_debug(const float *pts, int64_t n, const int *dims, const int *stride, int ce,
+                                          int32_t *cells, int32_t *piece, cudaStream_t st)
+{
+    ib::k_debug<SP><<<grid_for(n), kTPB, 0, st>>>(pts, n, make_vol<float>(nullptr, dims, stride, ce), cells, piece);
+    return cudaPeekAtLastError();
+}
+
+}  // namespace
+
+namespace ibr {
+
+void IB_CAT(fill_, INTERP_SPLINE, _, INTERP_PART)(SplineOps &o)
+{
+#if INTERP_PART == 3
+    o.name = SP::NAME;
+    o.s = SP::S;
+    o.nxi = SP::NXI;
+    o.M = SP::M;
+    o.D = SP::D;
+    o.detl = SP::DETL;
+    o.halo = SP::HALO;
+    o.K = SP::K;
+    o.deg = SP::DEG;
+    o.nmon = SP::NMON;
+    o.xi = &SP::XI[0][0];
+    o.cosets = &SP::COSET[0][0];
+    o.fma_value = SP::FMA_VALUE;
+    o.fma_grad = SP::FMA_GRAD;
+    o.lookups = SP::LOOKUPS;
+    o.adjoint = launch_adjoint;
+    o.debug = launch_debug;
+#else
+    constexpr int mode = INTERP_PART;
+    o.eval[0][mode] = launch_eval<float, mode>;
+    if constexpr (SP::HALF_STORAGE) {
+        o.eval[1][mode] = launch_eval<__half, mode>;
+        o.eval[2][mode] = launch_eval<__nv_bfloat16, mode>;
+    }
+#endif
+}
+
+}  // namespace ibr

@@ -1,0 +1,40 @@
+"""Built-in (lattice, direction matrix) pairs, in the paper's integer frame.
+
+Lattice generating matrices are those of Sec. 3 (L_BCC, L_FCC) and the D4* lattice
+Z^4 u (Z^4 + (1/2,1/2,1/2,1/2)) scaled by 2 so that it is an integer lattice (all coordinates of
+equal parity).  Direction matrices are the Table 1 rows of Sec. 5.1 and the 8-direction D4 spline
+of Sec. 5.2 (its sign convention is immaterial once the spline is centred).
+"""
+from __future__ import annotations
+
+L_CC = [[1, 0, 0], [0, 1, 0], [0, 0, 1]]
+L_BCC = [[-1, 1, 1], [1, -1, 1], [1, 1, -1]]          # Sec. 3
+L_FCC = [[0, 1, 1], [1, 0, 1], [1, 1, 0]]             # Sec. 3
+L_D4S = [[2, 0, 0, 1], [0, 2, 0, 1], [0, 0, 2, 1], [0, 0, 0, 1]]  # 2Z^4 u 2Z^4+(1,1,1,1)
+
+XI_BCC_RD = [[-1, 1, 1, -1], [1, -1, 1, -1], [1, 1, -1, -1]]      # Table 1, linear RD
+XI_FCC6 = [[1, -1, 1, 1, 0, 0], [1, 1, 0, 0, 1, -1], [0, 0, 1, -1, 1, 1]]   # Table 1, FCC 6-dir
+XI_CC7 = [[1, 0, 0, -1, 1, 1, -1], [0, 1, 0, 1, -1, 1, -1], [0, 0, 1, 1, 1, -1, -1]]  # Table 1, TRD
+XI_BCC_QUARTIC = [[2, 0, 0, -1, 1, 1, -1], [0, 2, 0, 1, -1, 1, -1], [0, 0, 2, 1, 1, -1, -1]]
+XI_D4 = [[1, 1, 1, 1, 1, 1, 1, 1],
+         [1, 1, 1, 1, -1, -1, -1, -1],
+         [1, 1, -1, -1, 1, 1, -1, -1],
+         [1, -1, 1, -1, 1, -1, 1, -1]]                # Sec. 5.2, 8 directions (1, +-1, +-1, +-1)
+
+
+def _twice(xi):
+    return [row + row for row in xi]
+
+
+CATALOG = {
+    "bcc_linear": (L_BCC, XI_BCC_RD),
+    "bcc_quintic": (L_BCC, _twice(XI_BCC_RD)),
+    "fcc_6dir": (L_FCC, XI_FCC6),
+    "cc_7dir": (L_CC, XI_CC7),
+    "d4s_8dir": (L_D4S, XI_D4),
+}
+
+
+def catalog_entry(name: str):
+    L, xi = CATALOG[name]
+    return [list(r) for r in L], [list(r) for r in xi]

@@ -1,0 +1,194 @@
+"""Emit the generator's tables as a C++ header consumed by the CUDA kernels, plus JSON metadata.
+
+    python -m paper_2102_08514_b300.gen.emit            # (re)writes csrc/generated/
+
+The header holds, per built-in spline, a struct of `static constexpr` tables: the coset shifts, the
+chamber planes and the sigma table (Sec. 4.2), and per piece its anchor, its gather stencil and the
+nonzero entries of its coefficient matrix A (monomial x site) in the nested-Horner monomial layout.
+Values are the exact rationals rounded once to FP32 and written as hexadecimal literals.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+from fractions import Fraction as Fr
+
+import numpy as np
+
+from .catalog import CATALOG
+from .pieces import analyse, horner_order, n_monomials
+
+GEN_VERSION = 1
+HERE = os.path.dirname(os.path.abspath(__file__))
+OUT_DIR = os.path.join(os.path.dirname(HERE), "csrc", "generated")
+# splines whose FP16 / BF16 coefficient-storage kernels are compiled (the 4-D spline's kernels are
+# large, so only its FP32 variant is built)
+HALF_STORAGE = {"bcc_linear", "bcc_quintic", "fcc_6dir", "cc_7dir"}
+
+
+def f32_hex(v) -> str:
+    x = float(np.float32(float(Fr(v))))
+    if x == 0.0:
+        return "0.0f"
+    return f"{x.hex()}f"
+
+
+def horner_fma_count(s, d):
+    """FMAs of the nested Horner evaluation of a dense polynomial of degree d in s variables."""
+    if s == 0:
+        return 0
+    return sum(horner_fma_count(s - 1, d - k) for k in range(d + 1)) + d
+
+
+def horner_grad_fma_count(s, d):
+    """FMAs of the nested Horner evaluation carrying the value and all s partial derivatives."""
+    if s == 0:
+        return 0
+    inner = sum(horner_grad_fma_count(s - 1, d - k) for k in range(d + 1))
+    # per step of the outer Horner: value (1), d/dt_1 (1), and s-1 inner partials (s-1)
+    return inner + d * (s + 1)
+
+
+def piece_volumes(T):
+    from scipy.spatial import ConvexHull
+    vols = []
+    for pc in T.pieces:
+        V = np.array([[float(a) for a in v] for v in pc.verts])
+        vols.append(ConvexHull(V).volume)
+    tot = sum(vols)
+    return [v / tot for v in vols]
+
+
+def _arr(vals, fmt=str):
+    return "{" + ", ".join(fmt(v) for v in vals) + "}"
+
+
+def emit_struct(T, half_storage: bool = True) -> tuple[str, dict]:
+    s = T.s
+    order = horner_order(s, T.degree)
+    index = {e: i for i, e in enumerate(order)}
+    nmon = n_monomials(s, T.degree)
+    K = len(T.pieces)
+    nsmax = max(len(pc.sites) for pc in T.pieces)
+    nz_lists = []
+    for pc in T.pieces:
+        nz = []
+        for m, P in enumerate(pc.polys):
+            for e, v in sorted(P.c.items(), key=lambda kv: index[kv[0]]):
+                nz.append((m, index[e], v))
+        nz_lists.append(nz)
+    nnzmax = max(len(z) for z in nz_lists)
+    Q = len(T.planes)
+    vols = piece_volumes(T)
+    hv = horner_fma_count(s, T.degree)
+    hg = horner_grad_fma_count(s, T.degree)
+    M = len(T.cosets)
+    fma_value = M * sum(w * (len(z) + hv) for w, z in zip(vols, nz_lists))
+    fma_grad = M * sum(w * (len(z) + hg) for w, z in zip(vols, nz_lists))
+    lookups = M * sum(w * len(pc.sites) for w, pc in zip(vols, T.pieces))
+
+    L = []
+    L.append(f"struct {T.name} {{")
+    L.append(f'    static constexpr const char* NAME = "{T.name}";')
+    L.append(f"    static constexpr int S = {s}, NXI = {len(T.xi[0])}, M = {M}, D = {T.D}, DETL = {T.det_l};")
+    L.append(f"    static constexpr int K = {K}, Q = {Q}, R = {T.r}, DEG = {T.degree}, NMON = {nmon}, HALO = {T.halo};")
+    L.append(f"    static constexpr int NSMAX = {nsmax}, NNZMAX = {nnzmax}, FOLD = {T.fold};")
+    L.append(f"    static constexpr bool HALF_STORAGE = {'true' if half_storage else 'false'};  // FP16/BF16 kernels built")
+    L.append(f"    static constexpr int XI[S][NXI] = {_arr([_arr(r) for r in T.xi])};")
+    L.append(f"    static constexpr int LMAT[S][S] = {_arr([_arr(r) for r in T.L])};")
+    L.append(f"    static constexpr int COSET[M][S] = {_arr([_arr(c) for c in T.cosets])};")
+    if Q:
+        L.append(f"    static constexpr int PLANE_P[Q][S] = {_arr([_arr(p) for p, _ in T.planes])};")
+        L.append(f"    static constexpr float PLANE_E[Q] = {_arr([e for _, e in T.planes], f32_hex)};")
+    else:
+        L.append("    static constexpr int PLANE_P[1][S] = {};")
+        L.append("    static constexpr float PLANE_E[1] = {0.0f};")
+    L.append(f"    static constexpr int SIGMA[R] = {_arr(T.sigma)};")
+    L.append(f"    static constexpr int NS[K] = {_arr([len(pc.sites) for pc in T.pieces])};")
+    L.append(f"    static constexpr int NNZ[K] = {_arr([len(z) for z in nz_lists])};")
+    L.append(f"    static constexpr float ANCHOR[K][S] = {_arr([_arr(pc.anchor, f32_hex) for pc in T.pieces])};")
+    sites = []
+    for pc in T.pieces:
+        rows = [_arr(g) for g in pc.sites] + [_arr([0] * s)] * (nsmax - len(pc.sites))
+        sites.append(_arr(rows))
+    L.append(f"    static constexpr signed char SITE[K][NSMAX][S] = {_arr(sites)};")
+    # nonzeros of A_j as a type list nz<site, monomial, value, first write of b[monomial],
+    # first entry of its site, last entry of its site>, grouped by site
+    for j, z in enumerate(nz_lists):
+        seen = set()
+        ents = []
+        for idx, (m, a, v) in enumerate(z):
+            sf = int(idx == 0 or z[idx - 1][0] != m)
+            sl = int(idx == len(z) - 1 or z[idx + 1][0] != m)
+            ents.append(f"nz<{m}, {a}, {f32_hex(v)}, {int(a not in seen)}, {sf}, {sl}>")
+            seen.add(a)
+        body = ",\n        ".join(", ".join(ents[i:i + 3]) for i in range(0, len(ents), 3))
+        L.append(f"    using NZ{j} = nzlist<\n        {body}>;")
+    L.append(f"    template <int J> using NZL = typename pick<J, {', '.join(f'NZ{j}' for j in range(K))}>::type;")
+    L.append(f"    static constexpr double FMA_VALUE = {fma_value!r}, FMA_GRAD = {fma_grad!r}, LOOKUPS = {lookups!r};")
+    L.append("};")
+
+    meta = dict(name=T.name, s=s, L=T.L, xi=T.xi, det_l=T.det_l, D=T.D, cosets=T.cosets, fold=T.fold,
+                degree=T.degree, n_monomials=nmon, halo=T.halo, r=T.r, sigma=T.sigma,
+                planes=[[list(p), str(e)] for p, e in T.planes],
+                pieces=[dict(anchor=[str(a) for a in pc.anchor], sites=pc.sites, code=pc.code,
+                             nnz=len(z), volume_fraction=w,
+                             vertices=[[str(a) for a in v] for v in pc.verts],
+                             ineqs=[[list(map(str, a)), str(b)] for a, b in pc.ineqs],
+                             polys=[{",".join(map(str, e)): str(v) for e, v in P.c.items()} for P in pc.polys])
+                        for pc, z, w in zip(T.pieces, nz_lists, vols)],
+                fma_value=fma_value, fma_grad=fma_grad, lookups=lookups,
+                horner_fma=hv, horner_grad_fma=hg)
+    return "\n".join(L), meta
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=OUT_DIR)
+    ap.add_argument("names", nargs="*", default=list(CATALOG))
+    args = ap.parse_args(argv)
+    os.makedirs(args.out, exist_ok=True)
+    structs, metas = [], {}
+    for name in args.names:
+        L, xi = CATALOG[name]
+        T = analyse(name, L, xi)
+        text, meta = emit_struct(T, half_storage=name in HALF_STORAGE)
+        structs.append(text)
+        metas[name] = meta
+    body = "\n\n".join(structs)
+    digest = hashlib.sha256(body.encode()).hexdigest()[:16]
+    hdr = [
+        "// Generated by paper_2102_08514_b300/gen/emit.py from the exact rational analysis of each",
+        "// spline (pieces, stencils, polynomial coefficients rounded once to FP32). Do not edit.",
+        f"// generator version {GEN_VERSION}, table digest {digest}",
+        "#pragma once",
+        "",
+        "namespace interp_gen {",
+        "",
+        "// one nonzero A[mon][site] = val of a piece's coefficient matrix; FIRST: first write of b[mon];",
+        "// SFIRST / SLAST: first / last nonzero of its site (the list is grouped by site)",
+        "template <int SITE, int MON, float VAL, int FIRST, int SFIRST, int SLAST> struct nz {};",
+        "template <class... Z> struct nzlist { static constexpr int size = sizeof...(Z); };",
+        "template <int J, class T0, class... Ts> struct pick { using type = typename pick<J - 1, Ts...>::type; };",
+        "template <class T0, class... Ts> struct pick<0, T0, Ts...> { using type = T0; };",
+        "",
+        body,
+        "",
+        "}  // namespace interp_gen",
+        "",
+        "// X-macro over every built-in spline: X(struct name)",
+        "#define INTERP_GEN_SPLINES(X) " + " ".join(f"X({n})" for n in args.names),
+        f'#define INTERP_GEN_DIGEST "{digest}"',
+        "",
+    ]
+    with open(os.path.join(args.out, "splines.h"), "w") as f:
+        f.write("\n".join(hdr))
+    with open(os.path.join(args.out, "splines.json"), "w") as f:
+        json.dump(dict(version=GEN_VERSION, digest=digest, splines=metas), f, indent=1)
+    print(f"wrote {len(args.names)} splines, digest {digest}")
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,525 @@
+"""Exact piecewise-polynomial analysis of phi(x) = |det L| M_Xi(x + sum(Xi)/2) per Cartesian coset.
+
+Steps (Horacsek & Alim, arXiv 2102.08514):
+
+1. Cartesian coset decomposition L Z^s = U_k (D Z^s + l_k) with G L = D = d I (Sec. 4.1).
+2. Region of evaluation: the cube [-D/2, D/2)^s centred on the nearest coset site, so the shift
+   rho(x) is a rounding (Sec. 4.1, the function rho).
+3. Symmetry fold: when every signed permutation S maps Xi onto itself up to column signs, phi is
+   invariant under S, and the cube folds onto the chamber D/2 >= y_1 >= ... >= y_s >= 0.  This is
+   the reflection trick of Sec. 4.2 taken to the whole signed-permutation group; the per-piece
+   change of variables (T, t, pi) of Sec. 4.3 becomes the per-query signed permutation S.
+4. Sub-regions: the mesh planes of Sec. 3 (hyperplanes spanned by (s-1)-subsets of Xi, through
+   every sum of a subset of the columns, shifted by D Z^s) that cut the chamber; their cells are the
+   sub-regions of evaluation S_j (Sec. 4.1), identified branch-free by plane sign bits q and the
+   table sigma[q mod r] with r found by brute force (Sec. 4.2).
+5. Per cell, the stencil C_0(S_j) (the coset sites whose shifted support covers the cell) and the
+   explicit polynomial of phi(y - D g) for every stencil site g (the functions psi_j of Sec. 4.1).
+   The polynomials are computed exactly (Fractions) by running de Boor's recurrence on polynomials
+   in y: inside one cell every sub-box-spline M_{Xi'}(y + v) is a single polynomial, and every
+   base-case decision is constant on the cell, so it is taken at an interior point.
+
+Everything here is exact rational arithmetic; the emitter rounds to FP32 only at the end.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+from dataclasses import dataclass, field
+from fractions import Fraction as Fr
+from functools import lru_cache
+
+
+# ----------------------------------------------------------------------------- exact linear algebra
+
+def det(m):
+    """Determinant of a small square matrix of ints/Fractions (Laplace expansion)."""
+    n = len(m)
+    if n == 1:
+        return m[0][0]
+    if n == 2:
+        return m[0][0] * m[1][1] - m[0][1] * m[1][0]
+    total = 0
+    for c in range(n):
+        if m[0][c] == 0:
+            continue
+        sub = [row[:c] + row[c + 1:] for row in m[1:]]
+        total += (-1) ** c * m[0][c] * det(sub)
+    return total
+
+
+def solve(A, b):
+    """Exact solution of A x = b (A square, nonsingular) by Gauss-Jordan over Fractions."""
+    n = len(A)
+    M = [[Fr(v) for v in A[r]] + [Fr(b[r])] for r in range(n)]
+    for c in range(n):
+        p = next(r for r in range(c, n) if M[r][c] != 0)
+        M[c], M[p] = M[p], M[c]
+        pv = M[c][c]
+        M[c] = [v / pv for v in M[c]]
+        for r in range(n):
+            if r != c and M[r][c] != 0:
+                f = M[r][c]
+                M[r] = [a - f * bb for a, bb in zip(M[r], M[c])]
+    return [M[r][n] for r in range(n)]
+
+
+def inverse(A):
+    n = len(A)
+    cols = [solve(A, [1 if i == j else 0 for i in range(n)]) for j in range(n)]
+    return [[cols[j][i] for j in range(n)] for i in range(n)]
+
+
+def rank(vectors, s):
+    rows = [[Fr(v) for v in vec] for vec in vectors]
+    r = 0
+    for c in range(s):
+        p = next((i for i in range(r, len(rows)) if rows[i][c] != 0), None)
+        if p is None:
+            continue
+        rows[r], rows[p] = rows[p], rows[r]
+        for i in range(len(rows)):
+            if i != r and rows[i][c] != 0:
+                f = rows[i][c] / rows[r][c]
+                rows[i] = [a - f * b for a, b in zip(rows[i], rows[r])]
+        r += 1
+    return r
+
+
+def hyperplane_normal(vectors, s):
+    """Primitive integer normal of the hyperplane spanned by s-1 integer vectors (None if they do
+    not span a hyperplane); sign fixed so that the first nonzero entry is positive."""
+    n = []
+    for i in range(s):
+        sub = [[v[k] for k in range(s) if k != i] for v in vectors]
+        n.append((-1) ** i * det(sub) if s > 1 else 1)
+    g = 0
+    for a in n:
+        g = math.gcd(g, abs(int(a)))
+    if g == 0:
+        return None
+    n = [int(a) // g for a in n]
+    for a in n:
+        if a != 0:
+            if a < 0:
+                n = [-b for b in n]
+            break
+    return tuple(n)
+
+
+# ----------------------------------------------------------------------------- lattice structure
+
+def coset_structure(L):
+    """D (with D Z^s inside L Z^s, D minimal) and the coset shifts l_k in [0, D)^s (Sec. 4.1)."""
+    s = len(L)
+    dl = det(L)
+    if dl == 0:
+        raise ValueError("L must have full rank")
+    Linv = inverse(L)
+
+    def member(z):
+        return all(sum(Linv[i][j] * z[j] for j in range(s)).denominator == 1 for i in range(s))
+
+    D = next(d for d in range(1, abs(dl) + 1)
+             if all(member([d if j == i else 0 for j in range(s)]) for i in range(s)))
+    cosets = [z for z in itertools.product(range(D), repeat=s) if member(z)]
+    assert len(cosets) * abs(dl) == D ** s, "coset count must be D^s / |det L|"
+    return D, [list(z) for z in cosets], abs(dl)
+
+
+def signed_permutation_invariant(xi):
+    """True if every signed permutation maps the columns of Xi onto themselves up to sign, i.e.
+    the centred box spline is invariant under the whole hyperoctahedral group."""
+    s = len(xi)
+    cols = [tuple(xi[a][j] for a in range(s)) for j in range(len(xi[0]))]
+
+    def canon(v):
+        for a in v:
+            if a != 0:
+                return tuple(v) if a > 0 else tuple(-b for b in v)
+        return tuple(v)
+
+    base = sorted(canon(c) for c in cols)
+    for perm in itertools.permutations(range(s)):
+        for signs in itertools.product((1, -1), repeat=s):
+            img = sorted(canon([signs[a] * c[perm[a]] for a in range(s)]) for c in cols)
+            if img != base:
+                return False
+    return True
+
+
+# ----------------------------------------------------------------------------- polynomials
+
+def n_monomials(s, d):
+    return math.comb(d + s, s)
+
+
+@lru_cache(maxsize=None)
+def horner_order(s, d):
+    """Monomial exponent tuples of total degree <= d in s variables, in the nested-Horner layout
+    the kernels use: P(t_1..t_s) = sum_k t_1^k P_k(t_2..t_s), with deg P_k <= d - k, stored as
+    P_0, P_1, ..., P_d, each recursively in the same layout."""
+    if s == 0:
+        return ((),)
+    out = []
+    for k in range(d + 1):
+        for rest in horner_order(s - 1, d - k):
+            out.append((k,) + rest)
+    return tuple(out)
+
+
+class Poly:
+    """Sparse polynomial with exact Fraction coefficients: {exponent tuple: Fraction}."""
+    __slots__ = ("c",)
+
+    def __init__(self, c=None):
+        self.c = c or {}
+
+    @staticmethod
+    def const(v, s):
+        return Poly({(0,) * s: Fr(v)}) if v != 0 else Poly()
+
+    def is_zero(self):
+        return not self.c
+
+    def add(self, other, scale=1):
+        out = dict(self.c)
+        for e, v in other.c.items():
+            w = out.get(e, 0) + scale * v
+            if w:
+                out[e] = w
+            else:
+                out.pop(e, None)
+        return Poly(out)
+
+    def scale(self, a):
+        if a == 0:
+            return Poly()
+        return Poly({e: v * a for e, v in self.c.items()})
+
+    def mul_affine(self, aff):
+        """Multiply by a0 + sum_a aff[1+a] y_a."""
+        s = len(aff) - 1
+        out = {}
+        for e, v in self.c.items():
+            if aff[0]:
+                w = out.get(e, 0) + v * aff[0]
+                out[e] = w
+            for a in range(s):
+                if aff[1 + a]:
+                    e2 = e[:a] + (e[a] + 1,) + e[a + 1:]
+                    out[e2] = out.get(e2, 0) + v * aff[1 + a]
+        return Poly({e: v for e, v in out.items() if v})
+
+    def taylor_shift(self, anchor):
+        """Return Q with Q(t) = P(t + anchor) (re-expansion about the anchor point)."""
+        s = len(anchor)
+        out = {}
+        for e, v in self.c.items():
+            # prod_a (t_a + anchor_a)^{e_a}
+            terms = [{(): v}]
+            for a in range(s):
+                nxt = {}
+                for pre, pv in terms[-1].items():
+                    for k in range(e[a] + 1):
+                        coef = pv * math.comb(e[a], k) * (anchor[a] ** (e[a] - k))
+                        if coef:
+                            key = pre + (k,)
+                            nxt[key] = nxt.get(key, 0) + coef
+                terms.append(nxt)
+            for key, cv in terms[-1].items():
+                out[key] = out.get(key, 0) + cv
+        return Poly({e: v for e, v in out.items() if v})
+
+    def __call__(self, y):
+        tot = Fr(0)
+        for e, v in self.c.items():
+            term = v
+            for a, k in enumerate(e):
+                if k:
+                    term *= Fr(y[a]) ** k
+            tot += term
+        return tot
+
+
+# ----------------------------------------------------------------------------- polytopes
+
+@dataclass
+class Cell:
+    """A convex polytope {y : a . y <= b for (a, b) in ineqs} with its exact vertices."""
+    ineqs: list
+    verts: list = field(default_factory=list)
+    signs: dict = field(default_factory=dict)   # plane index -> 0/1 side bit
+
+    def interior_point(self):
+        n = len(self.verts)
+        s = len(self.verts[0])
+        return [sum(v[a] for v in self.verts) / n for a in range(s)]
+
+
+def vertices(ineqs, s):
+    """Vertices of {a . y <= b} by brute force over s-subsets of the inequalities."""
+    vs = set()
+    for sub in itertools.combinations(range(len(ineqs)), s):
+        A = [ineqs[i][0] for i in sub]
+        if det(A) == 0:
+            continue
+        y = solve(A, [ineqs[i][1] for i in sub])
+        if all(sum(a[k] * y[k] for k in range(s)) <= b for a, b in ineqs):
+            vs.add(tuple(y))
+    return [list(v) for v in sorted(vs)]
+
+
+def split(cell, p, e, s, idx):
+    """Split a cell by the plane p . y = e if the plane passes through its interior."""
+    vals = [sum(p[k] * v[k] for k in range(s)) - e for v in cell.verts]
+    if not (any(v > 0 for v in vals) and any(v < 0 for v in vals)):
+        side = 1 if any(v > 0 for v in vals) else 0
+        cell.signs[idx] = side
+        return [cell]
+    out = []
+    for side, (a, b) in ((0, (list(p), e)), (1, ([-x for x in p], -e))):
+        ineqs = cell.ineqs + [(a, b)]
+        c = Cell(ineqs, vertices(ineqs, s), dict(cell.signs))
+        c.signs[idx] = side
+        out.append(c)
+    return out
+
+
+# ----------------------------------------------------------------------------- the analysis
+
+@dataclass
+class Piece:
+    anchor: list          # expansion point (exact rationals) of the piece polynomials
+    sites: list           # grid offsets g (ints): coset site D*g relative to the nearest site
+    polys: list           # exact Poly per site, in t = y - anchor
+    code: int             # plane sign bits q of the cell
+    verts: list           # exact vertices of the cell
+    ineqs: list           # exact H-representation of the cell
+
+
+@dataclass
+class SplineTables:
+    name: str
+    s: int
+    L: list
+    xi: list
+    det_l: int
+    D: int
+    cosets: list
+    fold: int             # 2: signed permutations, 0: none
+    degree: int
+    planes: list          # (p: tuple of ints, e: Fraction) in the folded frame
+    r: int
+    sigma: list           # sigma[q mod r] -> piece index (-1 unused)
+    pieces: list
+    halo: int             # max |g_a| over all stencil sites (grid units)
+    lookups: int = 0      # coefficient reads per query (all cosets)
+
+
+def _zonotope_halfwidths(cols, normals):
+    return {p: Fr(sum(abs(sum(p[a] * c[a] for a in range(len(p)))) for c in cols), 2) for p in normals}
+
+
+def analyse(name, L, xi, anchor_den=64, verbose=False):
+    """Run the analysis for phi = |det L| M_Xi(. + sum(Xi)/2) on the lattice L Z^s."""
+    s = len(xi)
+    n = len(xi[0])
+    cols = [tuple(int(xi[a][j]) for a in range(s)) for j in range(n)]
+    if rank(cols, s) != s:
+        raise ValueError("Xi must have rank s")
+    D, cosets, det_l = coset_structure(L)
+    Linv = inverse(L)
+    for c in cols:  # partition of unity on L needs L^{-1} Xi integer (Sec. 4.1)
+        if any(sum(Linv[i][j] * c[j] for j in range(s)).denominator != 1 for i in range(s)):
+            raise ValueError("L^{-1} Xi must be integer")
+    fold = 2 if signed_permutation_invariant(xi) else 0
+    centre = [Fr(sum(c[a] for c in cols), 2) for a in range(s)]
+    degree = n - s
+
+    # mesh plane normals and offsets (Sec. 3, the fine mesh Gamma)
+    normals = set()
+    for sub in itertools.combinations(cols, s - 1):
+        p = hyperplane_normal(list(sub), s)
+        if p is not None:
+            normals.add(p)
+    normals = sorted(normals)
+    offsets = {}
+    for p in normals:
+        dots = [sum(p[a] * c[a] for a in range(s)) for c in cols]
+        sums = {0}
+        for dv in dots:
+            sums |= {x + dv for x in sums}
+        pc = sum(p[a] * centre[a] for a in range(s))
+        offsets[p] = sorted({Fr(x) - pc for x in sums})
+
+    # region of evaluation, folded
+    half = Fr(D, 2)
+    if fold == 2:
+        chamber = [([-1 if k == s - 1 else 0 for k in range(s)], 0)]           # y_s >= 0
+        chamber += [([1 if k == 0 else 0 for k in range(s)], half)]             # y_1 <= D/2
+        for a in range(s - 1):                                                  # y_a >= y_{a+1}
+            chamber.append(([(-1 if k == a else (1 if k == a + 1 else 0)) for k in range(s)], 0))
+    else:
+        chamber = []
+        for a in range(s):
+            chamber.append(([1 if k == a else 0 for k in range(s)], half))
+            chamber.append(([-1 if k == a else 0 for k in range(s)], half))
+    root = Cell(chamber, vertices(chamber, s))
+
+    # planes p . y = e + D m (m integer) cutting the chamber interior
+    planes = []
+    for p in normals:
+        vals = [sum(p[a] * v[a] for a in range(s)) for v in root.verts]
+        lo, hi = min(vals), max(vals)
+        for o in offsets[p]:
+            k = math.floor((lo - o) / D)
+            while o + D * k <= hi:
+                e = o + D * k
+                if lo < e < hi:
+                    sg = [sum(p[a] * v[a] for a in range(s)) - e for v in root.verts]
+                    if any(x > 0 for x in sg) and any(x < 0 for x in sg):
+                        planes.append((p, e))
+                k += 1
+    planes = sorted(set(planes))
+
+    cells = [root]
+    for idx, (p, e) in enumerate(planes):
+        nxt = []
+        for c in cells:
+            nxt.extend(split(c, p, e, s, idx))
+        cells = nxt
+    if verbose:
+        print(f"{name}: s={s} n={n} D={D} cosets={len(cosets)} fold={fold} Q={len(planes)} cells={len(cells)}")
+
+    halfw = _zonotope_halfwidths(cols, normals)
+    bbox = [Fr(sum(abs(c[a]) for c in cols), 2) for a in range(s)]
+
+    pieces = []
+    for c in cells:
+        z = c.interior_point()
+        # stencil: coset sites D g whose open support contains the cell (test at an interior point)
+        rng = [range(math.floor((z[a] - bbox[a]) / D), math.ceil((z[a] + bbox[a]) / D) + 1) for a in range(s)]
+        sites = []
+        for g in itertools.product(*rng):
+            w = [z[a] - D * g[a] for a in range(s)]
+            if all(abs(sum(p[a] * w[a] for a in range(s))) < halfw[p] for p in normals):
+                sites.append(list(g))
+        polys = _piece_polynomials(cols, s, det_l, centre, D, z, sites)
+        anchor = [Fr(round(z[a] * anchor_den), anchor_den) for a in range(s)]
+        polys = [P.taylor_shift(anchor) for P in polys]
+        code = sum((c.signs[i] << i) for i in range(len(planes)))
+        pieces.append(Piece(anchor, sites, polys, code, c.verts, c.ineqs))
+
+    codes = [pc.code for pc in pieces]
+    Q = len(planes)
+
+    def nearest(q):
+        # a sign code no cell has (rounding near where several planes meet): the piece whose code
+        # differs in the fewest plane bits, which is a piece meeting at that corner
+        return min(range(len(codes)), key=lambda j: (bin(q ^ codes[j]).count("1"), j))
+
+    if Q <= 4:
+        # small Q: index sigma by q directly (r = 2^Q), every code mapped to a real piece
+        r = 1 << Q
+        sigma = [nearest(q) for q in range(r)]
+    else:
+        # Sec. 4.2: compress [0, 2^Q) to [0, r) by q mod r, r the smallest value separating the
+        # cells' codes (brute force)
+        r = next(r for r in range(len(codes), 1 << Q) if len({q % r for q in codes}) == len(codes))
+        sigma = [-1] * r
+        for j, q in enumerate(codes):
+            sigma[q % r] = j
+        for i in range(r):
+            if sigma[i] < 0:
+                sigma[i] = nearest(i)
+    halo = max((abs(g[a]) for pc in pieces for g in pc.sites for a in range(s)), default=0)
+    lookups = max(len(pc.sites) for pc in pieces) * len(cosets)
+    return SplineTables(name, s, [list(r_) for r_ in L], [list(r_) for r_ in xi], det_l, D, cosets,
+                        fold, degree, planes, r, sigma, pieces, halo, lookups)
+
+
+def _piece_polynomials(cols, s, det_l, centre, D, z, sites):
+    """Exact polynomials of phi(y - D g), y in the cell around the interior point z, for every g.
+
+    M_{Xi'}(y + v) is computed by de Boor's recurrence on polynomials in y with t supported on a
+    basis B of Xi' (t_xi = 0 off B), so (n'-s) M = sum_{xi in B} [M1 + t_xi (M0 - M1)]
+    + sum_{xi not in B} M1 with M0 = M_{Xi'\\xi}(y + v), M1 = M_{Xi'\\xi}(y + v - xi).
+    Memoised on (columns left, v), shared by all sites of the cell.
+    """
+    n = len(cols)
+    memo = {}
+    spans = {}
+    basis_inv = {}
+    bb = {}
+
+    def spans_of(mask):
+        if mask not in spans:
+            vecs = [cols[j] for j in range(n) if mask >> j & 1]
+            spans[mask] = len(vecs) >= s and rank(vecs, s) == s
+        return spans[mask]
+
+    def box(mask):
+        if mask not in bb:
+            lo = [sum(min(0, cols[j][a]) for j in range(n) if mask >> j & 1) for a in range(s)]
+            hi = [sum(max(0, cols[j][a]) for j in range(n) if mask >> j & 1) for a in range(s)]
+            bb[mask] = (lo, hi)
+        return bb[mask]
+
+    def basis(mask):
+        if mask not in basis_inv:
+            idx = [j for j in range(n) if mask >> j & 1]
+            for sub in itertools.combinations(idx, s):
+                B = [[cols[j][a] for j in sub] for a in range(s)]
+                dB = det(B)
+                if dB != 0:
+                    basis_inv[mask] = (sub, inverse(B), dB)
+                    break
+        return basis_inv[mask]
+
+    def M(mask, v):
+        key = (mask, v)
+        if key in memo:
+            return memo[key]
+        w = [z[a] + v[a] for a in range(s)]
+        lo, hi = box(mask)
+        if any(w[a] < lo[a] or w[a] > hi[a] for a in range(s)) or not spans_of(mask):
+            memo[key] = Poly()
+            return memo[key]
+        cnt = bin(mask).count("1")
+        sub, Binv, dB = basis(mask)
+        if cnt == s:
+            lam = [sum(Binv[i][a] * w[a] for a in range(s)) for i in range(s)]
+            if any(l == 0 or l == 1 for l in lam):
+                raise RuntimeError("interior point lies on a base-case facet")
+            inside = all(0 < l < 1 for l in lam)
+            memo[key] = Poly.const(Fr(1, abs(dB)) if inside else 0, s)
+            return memo[key]
+        acc = Poly()
+        for j in range(n):
+            if not mask >> j & 1:
+                continue
+            rest = mask & ~(1 << j)
+            if not spans_of(rest):
+                continue
+            v1 = tuple(v[a] - cols[j][a] for a in range(s))
+            M1 = M(rest, v1)
+            if j in sub:
+                i = sub.index(j)
+                # t_j(y) = sum_a Binv[i][a] (y_a + v_a)
+                aff = [sum(Binv[i][a] * v[a] for a in range(s))] + [Binv[i][a] for a in range(s)]
+                M0 = M(rest, v)
+                diff = M0.add(M1, -1)
+                acc = acc.add(M1).add(diff.mul_affine(aff))
+            else:
+                acc = acc.add(M1)
+        res = acc.scale(Fr(1, cnt - s))
+        memo[key] = res
+        return res
+
+    full = (1 << n) - 1
+    out = []
+    for g in sites:
+        v = tuple(Fr(centre[a]) - D * g[a] for a in range(s))
+        out.append(M(full, v).scale(det_l))
+    return out

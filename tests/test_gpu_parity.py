@@ -1,0 +1,230 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle, element by element.
+
+Tolerances (the benchmark spec): cell indices bit-exact; piece indices exact or within 1e-6 of a piece
+boundary; values max-abs <= 2e-6 * max|c|; gradients <= 2e-6 * max|c| * G with
+G = max_x sum_n |grad phi(x - n)|_inf estimated by the oracle; adjoint per coefficient <= 4e-6 *
+sum_q |g_q| phi(x_q - n) + 1e-7 (FP32 atomics in arbitrary order).
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import LATTICES, SPLINES, WORKLOADS, coefficients, interior_box, make_rng, uniform_points
+
+from _gpu_common import VALUE_TOL, grad_bound, mixed_points, require_cuda, spline_setup, tables
+
+pytestmark = pytest.mark.gpu
+
+SPLINES_ALL = ["bcc_linear", "bcc_quintic", "fcc_6dir", "cc_7dir", "d4s_8dir"]
+# small cases the oracle finishes in seconds, spanning several thread blocks and a ragged tail
+SMALL = {"bcc_linear": (12, 4133), "bcc_quintic": (12, 2085), "fcc_6dir": (10, 3011), "cc_7dir": (14, 2107),
+         "d4s_8dir": (7, 1093)}
+
+
+def _interp(name, dims, storage="f32"):
+    torch = require_cuda()
+    from paper_2102_08514_b300.binding import Interpolator
+    sp, lat, xi, detl = spline_setup(name)
+    return torch, Interpolator(np.asarray(lat.L), xi, dims, storage)
+
+
+def _coeffs(name, dims, seed):
+    lat = LATTICES[SPLINES[name].lattice]
+    rng = make_rng(seed, 3)
+    return rng.uniform(-1, 1, (len(lat.cosets),) + tuple(dims)).astype(np.float32)
+
+
+@pytest.mark.parametrize("name", SPLINES_ALL)
+def test_value_parity_small(name):
+    n_axis, nq = SMALL[name]
+    sp, lat, xi, detl = spline_setup(name)
+    dims = (n_axis,) * xi.shape[0]
+    torch, itp = _interp(name, dims)
+    c = _coeffs(name, dims, 1)
+    itp.set_coeffs(torch.from_numpy(c).cuda())
+    pts = mixed_points(name, dims, nq, 2)
+    got = itp.eval(torch.from_numpy(pts).cuda()).cpu().numpy()
+    ref = oracle.eval_sum(oracle.Spline(xi, detl), lat.D, lat.cosets, c.astype(np.float64), pts.astype(np.float64))
+    err = np.abs(got - ref)
+    assert err.max() <= VALUE_TOL * np.abs(c).max(), (err.max(), int(err.argmax()))
+
+
+@pytest.mark.parametrize("name", SPLINES_ALL)
+def test_cell_and_piece_indices(name):
+    n_axis, nq = SMALL[name]
+    sp, lat, xi, detl = spline_setup(name)
+    s = xi.shape[0]
+    dims = (n_axis,) * s
+    torch, itp = _interp(name, dims)
+    pts = mixed_points(name, dims, nq, 3)
+    cells, piece = itp.debug_indices(torch.from_numpy(pts).cuda())
+    cells = cells.cpu().numpy()
+    piece = piece.cpu().numpy()
+    ref_cells, offs = oracle.cells(s, lat.D, lat.cosets, pts.astype(np.float64))
+    assert np.array_equal(cells, ref_cells)
+    # the GPU's piece label j must name a polytope containing the oracle's folded offset
+    tab = tables()[name]
+    yf = oracle.folded_offsets(offs)
+    polys = []
+    for pc in tab["pieces"]:
+        A = np.array([[float(Fraction(a)) for a in row[0]] for row in pc["ineqs"]])
+        b = np.array([float(Fraction(row[1])) for row in pc["ineqs"]])
+        polys.append((A / np.linalg.norm(A, axis=1, keepdims=True), b / np.linalg.norm(A, axis=1)))
+    bad = 0
+    for q in range(len(pts)):
+        for k in range(len(lat.cosets)):
+            A, b = polys[piece[q, k]]
+            viol = (A @ yf[q, k] - b).max()
+            bad += viol > 1e-6
+    assert bad == 0
+
+
+@pytest.mark.parametrize("name", SPLINES_ALL)
+def test_gradient_parity(name):
+    n_axis, nq = SMALL[name]
+    sp, lat, xi, detl = spline_setup(name)
+    s = xi.shape[0]
+    dims = (n_axis,) * s
+    torch, itp = _interp(name, dims)
+    c = _coeffs(name, dims, 4)
+    itp.set_coeffs(torch.from_numpy(c).cuda())
+    lo, hi = interior_box(name, dims)
+    pts = uniform_points(make_rng(5, 0), nq // 2, lo, hi)
+    val, grad = itp.eval_grad(torch.from_numpy(pts).cuda())
+    sp_o = oracle.Spline(xi, detl)
+    ref_v, ref_g = oracle.eval_sum(sp_o, lat.D, lat.cosets, c.astype(np.float64), pts.astype(np.float64), grad=True)
+    G = grad_bound(name, pts[:32])
+    cmax = np.abs(c).max()
+    assert np.abs(val.cpu().numpy() - ref_v).max() <= VALUE_TOL * cmax
+    gerr = np.abs(grad.cpu().numpy() - ref_g).max()
+    assert gerr <= VALUE_TOL * cmax * G, (gerr, G)
+
+
+@pytest.mark.parametrize("name", SPLINES_ALL)
+def test_adjoint_parity(name):
+    n_axis, nq = SMALL[name]
+    sp, lat, xi, detl = spline_setup(name)
+    s = xi.shape[0]
+    dims = (n_axis,) * s
+    torch, itp = _interp(name, dims)
+    pts = mixed_points(name, dims, nq, 6)
+    g = make_rng(7, 0).uniform(-1, 1, len(pts)).astype(np.float32)
+    shape = (len(lat.cosets),) + dims
+    dpre = make_rng(8, 0).uniform(-1, 1, shape).astype(np.float32)      # accumulated into (+=)
+    dc = torch.from_numpy(dpre.copy()).cuda()
+    itp.backward(torch.from_numpy(pts).cuda(), torch.from_numpy(g).cuda(), dc)
+    sp_o = oracle.Spline(xi, detl)
+    ref = oracle.adjoint(sp_o, lat.D, lat.cosets, shape, pts.astype(np.float64), g.astype(np.float64))
+    bound = oracle.adjoint(sp_o, lat.D, lat.cosets, shape, pts.astype(np.float64), np.abs(g).astype(np.float64))
+    err = np.abs(dc.cpu().numpy() - dpre - ref)
+    assert np.all(err <= 4e-6 * bound + 1e-7), (err.max(), bound.max())
+
+
+@pytest.mark.parametrize("name", ["bcc_quintic", "fcc_6dir"])
+def test_pullback_dpts(name):
+    n_axis, nq = SMALL[name]
+    sp, lat, xi, detl = spline_setup(name)
+    dims = (n_axis,) * xi.shape[0]
+    torch, itp = _interp(name, dims)
+    c = _coeffs(name, dims, 9)
+    itp.set_coeffs(torch.from_numpy(c).cuda())
+    lo, hi = interior_box(name, dims)
+    pts = torch.from_numpy(uniform_points(make_rng(10, 0), 1000, lo, hi)).cuda()
+    g = torch.linspace(-1, 1, 1000, device="cuda")
+    _, grad = itp.eval_grad(pts)
+    dpts = torch.empty_like(grad)
+    from paper_2102_08514_b300.binding import interp_backward
+    interp_backward(itp.handle, pts, g, None, dpts)      # dcoeffs = NULL: dpts only
+    assert torch.allclose(dpts, g[:, None] * grad, rtol=1e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("name", ["bcc_quintic", "cc_7dir", "fcc_6dir"])
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_reduced_precision_storage(name, storage):
+    # stated accuracy: against the oracle on the dequantised coefficients the FP32 arithmetic
+    # bound holds; against the original coefficients the quantisation error dominates
+    n_axis, nq = SMALL[name]
+    sp, lat, xi, detl = spline_setup(name)
+    dims = (n_axis,) * xi.shape[0]
+    torch, itp = _interp(name, dims, storage)
+    c = _coeffs(name, dims, 11)
+    tdt = torch.float16 if storage == "f16" else torch.bfloat16
+    cq = torch.from_numpy(c).to(tdt)
+    itp.set_coeffs(cq.cuda())
+    lo, hi = interior_box(name, dims)
+    pts = uniform_points(make_rng(12, 0), nq // 2, lo, hi)
+    got = itp.eval(torch.from_numpy(pts).cuda()).cpu().numpy()
+    sp_o = oracle.Spline(xi, detl)
+    ref_q = oracle.eval_sum(sp_o, lat.D, lat.cosets, cq.double().numpy(), pts.astype(np.float64))
+    ref = oracle.eval_sum(sp_o, lat.D, lat.cosets, c.astype(np.float64), pts.astype(np.float64))
+    assert np.abs(got - ref_q).max() <= VALUE_TOL * np.abs(c).max()
+    unit = 2.0 ** -11 if storage == "f16" else 2.0 ** -8
+    assert np.abs(got - ref).max() <= 2 * unit * np.abs(c).max()
+
+
+def test_edge_cases():
+    torch = require_cuda()
+    name = "bcc_quintic"
+    dims = (8, 8, 8)
+    _, itp = _interp(name, dims)
+    c = _coeffs(name, dims, 13)
+    itp.set_coeffs(torch.from_numpy(c).cuda())
+    # empty input
+    out = torch.empty(0, device="cuda")
+    from paper_2102_08514_b300.binding import interp_eval
+    interp_eval(itp.handle, torch.empty(0, 3, device="cuda"), out)
+    # NaN / inf propagate; far away is exactly zero
+    p = torch.tensor([[float("nan"), 3.0, 3.0], [3.0, float("inf"), 3.0], [1e6, 1e6, 1e6], [-1e30, 0.0, 0.0]],
+                     device="cuda")
+    v = itp.eval(p).cpu().numpy()
+    assert np.isnan(v[0]) and np.isnan(v[1]) and v[2] == 0.0 and v[3] == 0.0
+    # host coefficients (F64 source) equal device F32 source after rounding
+    itp2 = _interp(name, dims)[1]
+    itp2.set_coeffs(torch.from_numpy(c.astype(np.float64)))
+    lo, hi = interior_box(name, dims)
+    q = torch.from_numpy(uniform_points(make_rng(14, 0), 777, lo, hi)).cuda()
+    assert torch.equal(itp.eval(q), itp2.eval(q))
+
+
+def test_create_rejects_bad_input():
+    require_cuda()
+    from paper_2102_08514_b300.binding import InterpError, interp_create, INTERP_EUNSUPPORTED, INTERP_EINVAL
+    sp, lat, xi, detl = spline_setup("bcc_quintic")
+    with pytest.raises(InterpError) as e:
+        interp_create(np.asarray(lat.L), xi[:, :5], (8, 8, 8))
+    assert e.value.status == INTERP_EUNSUPPORTED
+    with pytest.raises(InterpError) as e:
+        interp_create(np.zeros((3, 3)), xi, (8, 8, 8))
+    assert e.value.status == INTERP_EINVAL
+    # column order and signs do not matter
+    perm = np.random.default_rng(0).permutation(xi.shape[1])
+    h = interp_create(np.asarray(lat.L), -xi[:, perm], (8, 8, 8))
+    from paper_2102_08514_b300.binding import interp_destroy
+    interp_destroy(h)
+
+
+def test_full_size_headline_workload_sampled():
+    """BCC quintic on 2 x 128^3 FP32 signal samples with 2^24 queries, in the bench's launch
+    configuration; sampled outputs against the oracle."""
+    torch = require_cuda()
+    wl = WORKLOADS["bcc_quintic_128"]
+    sp, lat, xi, detl = spline_setup(wl.spline)
+    _, itp = _interp(wl.spline, wl.dims)
+    c = coefficients(wl)
+    itp.set_coeffs(torch.from_numpy(c).cuda())
+    lo, hi = interior_box(wl.spline, wl.dims)
+    pts = uniform_points(make_rng(wl.seed, 0), wl.queries, lo, hi)
+    dp = torch.from_numpy(pts).cuda()
+    val, grad = itp.eval_grad(dp)
+    v0 = itp.eval(dp)
+    idx = make_rng(wl.seed, 99).choice(wl.queries, 512, replace=False)
+    sp_o = oracle.Spline(xi, detl)
+    ref_v, ref_g = oracle.eval_sum(sp_o, lat.D, lat.cosets, c.astype(np.float64), pts[idx].astype(np.float64),
+                                   grad=True)
+    cmax = np.abs(c).max()
+    G = grad_bound(wl.spline, pts[idx[:32]])
+    assert np.abs(v0.cpu().numpy()[idx] - ref_v).max() <= VALUE_TOL * cmax
+    assert np.abs(val.cpu().numpy()[idx] - ref_v).max() <= VALUE_TOL * cmax
+    assert np.abs(grad.cpu().numpy()[idx] - ref_g).max() <= VALUE_TOL * cmax * G
