@@ -279,15 +279,17 @@ def cpu_baseline(wl, pts, c, seconds=15.0):
     orc, spl, lat = _oracle_setup(wl)
     cores = os.cpu_count() or 1
     cd = c.astype(np.float64)
-    probe = pts[:max(cores, 16)].astype(np.float64)
-    t = time.perf_counter()
-    orc.eval_sum(spl, lat.D, lat.cosets, cd, probe, grad=True, nthreads=cores)
-    rate = len(probe) / max(time.perf_counter() - t, 1e-6)
-    m = int(min(len(pts), max(cores, rate * seconds)))
-    sample = pts[len(probe):len(probe) + m].astype(np.float64)
-    t = time.perf_counter()
-    orc.eval_sum(spl, lat.D, lat.cosets, cd, sample, grad=True, nthreads=cores)
-    dt = time.perf_counter() - t
+    # grow the sample until it takes about `seconds` (bounded), then report the last one
+    m, off = 4 * cores, 0
+    while True:
+        sample = pts[off:off + m].astype(np.float64)
+        t = time.perf_counter()
+        orc.eval_sum(spl, lat.D, lat.cosets, cd, sample, grad=True, nthreads=cores)
+        dt = time.perf_counter() - t
+        off += m
+        if dt >= 0.5 * seconds or off + 2 * m > len(pts):
+            break
+        m = int(min(len(pts) - off, m * max(2.0, min(8.0, seconds / max(dt, 1e-3)))))
     return {"value": m / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{m} of the {wl.queries} queries (value+grad, FP64, brute-force recurrence), {dt:.1f} s"}
 
@@ -336,8 +338,8 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

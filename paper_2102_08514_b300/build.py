@@ -20,7 +20,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 OUT = os.path.join(BUILD, "libinterp_b300.so")
 GEN_HDR = os.path.join(CSRC, "generated", "splines.h")
-COMMON_DEPS = [os.path.join(CSRC, f) for f in ("kernels.cuh", "registry.h", "ops_inst.cu", "interp.cu")] + \
+COMMON_DEPS = [os.path.join(CSRC, f) for f in ("kernels.cuh", "registry.h", "layout.h", "ops_inst.cu", "interp.cu")] + \
     [GEN_HDR, os.path.join(ROOT, "include", "interp.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -48,58 +48,46 @@ const std::vector<SplineOps> &registry()
 template <class ST, class CT>
 __device__ __forceinline__ CT convert_to(ST x)
 {
-    float f;
-    if constexpr (std::is_same_v<ST, __half>) f = __half2float(x);
-    else if constexpr (std::is_same_v<ST, __nv_bfloat16>) f = __bfloat162float(x);
-    else if constexpr (std::is_same_v<ST, double>) {
+    if constexpr (std::is_same_v<ST, double>) {
+        // round once, directly from FP64 to the storage type
         if constexpr (std::is_same_v<CT, float>) return (float)x;
         else if constexpr (std::is_same_v<CT, __half>) return __double2half(x);
         else return __double2bfloat16(x);
-    } else f = x;
-    if constexpr (std::is_same_v<CT, float>) return f;
-    else if constexpr (std::is_same_v<CT, __half>) return __float2half_rn(f);
-    else return __float2bfloat16_rn(f);
+    } else {
+        float f;
+        if constexpr (std::is_same_v<ST, __half>) f = __half2float(x);
+        else if constexpr (std::is_same_v<ST, __nv_bfloat16>) f = __bfloat162float(x);
+        else f = x;
+        if constexpr (std::is_same_v<CT, float>) return f;
+        else if constexpr (std::is_same_v<CT, __half>) return __float2half_rn(f);
+        else return __float2bfloat16_rn(f);
+    }
 }
 
-// copy src (unpadded, coset-major, row-major) into the interior of the padded arrays
-template <class ST, class CT>
-__global__ void k_pad_copy(const ST *__restrict__ src, CT *__restrict__ dst, int64_t total, int s, int4 n, int4 stride,
-                           int coset_elems, int pad)
+// padded, bricked element offset of unpadded linear element e (coset-major, row-major)
+__device__ __forceinline__ int padded_offset(const ibl::Layout &L, int64_t e)
 {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = e;
-        int idx[4] = {0, 0, 0, 0};
-        const int nn[4] = {n.x, n.y, n.z, n.w};
-        for (int a = s - 1; a >= 0; --a) {
-            idx[a] = (int)(r % nn[a]);
-            r /= nn[a];
-        }
-        const int k = (int)r;
-        const int st[4] = {stride.x, stride.y, stride.z, stride.w};
-        int64_t off = (int64_t)k * coset_elems;
-        for (int a = 0; a < s; ++a) off += (int64_t)(idx[a] + pad) * st[a];
-        dst[off] = convert_to<ST, CT>(src[e]);
+    int p[4] = {0, 0, 0, 0};
+    for (int a = L.s - 1; a >= 0; --a) {
+        p[a] = (int)(e % L.n[a]) + L.pad;
+        e /= L.n[a];
     }
+    return ibl::elem_offset(L, (int)e, p);
+}
+
+// copy src (unpadded, coset-major, row-major) into the interior of the padded, bricked arrays
+template <class ST, class CT>
+__global__ void k_pad_copy(const ST *__restrict__ src, CT *__restrict__ dst, int64_t total, ibl::Layout L)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+        dst[padded_offset(L, e)] = convert_to<ST, CT>(src[e]);
 }
 
 // dst (unpadded FP32) += interior of the padded FP32 gradient buffer
-__global__ void k_unpad_add(const float *__restrict__ pad_buf, float *__restrict__ dst, int64_t total, int s, int4 n,
-                            int4 stride, int coset_elems, int pad)
+__global__ void k_unpad_add(const float *__restrict__ pad_buf, float *__restrict__ dst, int64_t total, ibl::Layout L)
 {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = e;
-        int idx[4] = {0, 0, 0, 0};
-        const int nn[4] = {n.x, n.y, n.z, n.w};
-        for (int a = s - 1; a >= 0; --a) {
-            idx[a] = (int)(r % nn[a]);
-            r /= nn[a];
-        }
-        const int k = (int)r;
-        const int st[4] = {stride.x, stride.y, stride.z, stride.w};
-        int64_t off = (int64_t)k * coset_elems;
-        for (int a = 0; a < s; ++a) off += (int64_t)(idx[a] + pad) * st[a];
-        dst[e] += pad_buf[off];
-    }
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] += pad_buf[padded_offset(L, e)];
 }
 
 // ------------------------------------------------------------------------------------ exact integer helpers
@@ -217,14 +205,12 @@ struct interp {
     const SplineOps *ops = nullptr;
     int s = 0;
     int dims[4] = {1, 1, 1, 1};
-    int pdims[4] = {1, 1, 1, 1};
-    int stride[4] = {0, 0, 0, 0};
-    int coset_elems = 0;
-    int64_t padded_total = 0;  // elements over all cosets
+    ibl::Layout lay{};         // layout of the stored coefficients (storage element size)
+    ibl::Layout lay32{};       // FP32 layout of the adjoint's padded gradient buffer
     int64_t coeff_count = 0;   // unpadded elements over all cosets
     interp_dtype storage = INTERP_F32;
-    void *coeffs = nullptr;    // padded storage
-    float *dpad = nullptr;     // padded FP32 gradient buffer (lazily allocated by interp_backward)
+    void *coeffs = nullptr;    // padded, bricked storage
+    float *dpad = nullptr;     // padded FP32 gradient buffer (allocated by the first interp_backward)
     int device = 0;
 };
 
@@ -287,29 +273,22 @@ interp_status interp_create(int s, const int32_t *L, const int32_t *xi, int n, c
     h->s = s;
     h->storage = storage;
     const int pad = 2 * ops->halo;
-    int64_t ce = 1, cc = 1;
+    int64_t cc = 1;
     for (int a = 0; a < s; ++a) {
         h->dims[a] = dims[a];
-        h->pdims[a] = dims[a] + 2 * pad;
-        ce *= h->pdims[a];
         cc *= dims[a];
     }
-    int64_t st = 1;
-    for (int a = s - 1; a >= 0; --a) {
-        h->stride[a] = (int)st;
-        st *= h->pdims[a];
-    }
-    if (ce * ops->M >= (int64_t)INT32_MAX) {
+    const int esz = storage == INTERP_F32 ? 4 : 2;
+    if (!ibl::make_layout(h->lay, s, h->dims, pad, esz, ops->M) ||
+        !ibl::make_layout(h->lay32, s, h->dims, pad, 4, ops->M)) {
         delete h;
         return INTERP_ESIZE;
     }
-    h->coset_elems = (int)ce;
-    h->padded_total = ce * ops->M;
     h->coeff_count = cc * ops->M;
     cudaGetDevice(&h->device);
-    const size_t esz = storage == INTERP_F32 ? 4 : 2;
-    cudaError_t e = cudaMalloc(&h->coeffs, (size_t)h->padded_total * esz);
-    if (e == cudaSuccess) e = cudaMemset(h->coeffs, 0, (size_t)h->padded_total * esz);
+    const size_t bytes = (size_t)h->lay.coset_elems * ops->M * esz;
+    cudaError_t e = cudaMalloc(&h->coeffs, bytes);
+    if (e == cudaSuccess) e = cudaMemset(h->coeffs, 0, bytes);
     if (e != cudaSuccess) {
         cudaFree(h->coeffs);
         delete h;
@@ -372,12 +351,9 @@ interp_status interp_set_coeffs(interp_t *h, const void *src, interp_dtype src_d
         }
         dsrc = tmp;
     }
-    const int pad = 2 * h->ops->halo;
-    const int4 n = make_int4(h->dims[0], h->dims[1], h->dims[2], h->dims[3]);
-    const int4 sd = make_int4(h->stride[0], h->stride[1], h->stride[2], h->stride[3]);
     const unsigned grid = (unsigned)std::min<int64_t>((h->coeff_count + 255) / 256, 148 * 32);
 #define PADCOPY(ST, CT) \
-    k_pad_copy<ST, CT><<<grid, 256, 0, st>>>(static_cast<const ST *>(dsrc), static_cast<CT *>(h->coeffs), h->coeff_count, h->s, n, sd, h->coset_elems, pad)
+    k_pad_copy<ST, CT><<<grid, 256, 0, st>>>(static_cast<const ST *>(dsrc), static_cast<CT *>(h->coeffs), h->coeff_count, h->lay)
 #define PADCOPY_SRC(CT)                                              \
     switch (src_dtype) {                                             \
     case INTERP_F32: PADCOPY(float, CT); break;                      \
@@ -414,7 +390,7 @@ static interp_status eval_common(const interp_t *h, const float *pts, int64_t np
     if (mode == 2 && !gout) return INTERP_EINVAL;
     if (npts > (int64_t)INT32_MAX * kTPB) return INTERP_ESIZE;
     const int dt = h->storage == INTERP_F32 ? 0 : (h->storage == INTERP_F16 ? 1 : 2);
-    cudaError_t e = h->ops->eval[dt][mode](pts, npts, h->coeffs, h->dims, h->stride, h->coset_elems, out, grad, gout,
+    cudaError_t e = h->ops->eval[dt][mode](pts, npts, h->coeffs, h->lay, out, grad, gout,
                                            static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) cudaGetLastError();
     return cuda_status(e);
@@ -444,22 +420,20 @@ interp_status interp_backward(interp_t *h, const float *pts, int64_t npts, const
     }
     if (!dcoeffs) return INTERP_OK;
     cudaError_t e = cudaSuccess;
+    const size_t dbytes = (size_t)h->lay32.coset_elems * h->ops->M * sizeof(float);
     if (!h->dpad) {
-        e = cudaMalloc(&h->dpad, (size_t)h->padded_total * sizeof(float));
+        e = cudaMalloc(&h->dpad, dbytes);
         if (e != cudaSuccess) {
             h->dpad = nullptr;
             cudaGetLastError();
             return cuda_status(e);
         }
     }
-    e = cudaMemsetAsync(h->dpad, 0, (size_t)h->padded_total * sizeof(float), st);
-    if (e == cudaSuccess) e = h->ops->adjoint(pts, npts, gout, h->dims, h->stride, h->coset_elems, h->dpad, st);
+    e = cudaMemsetAsync(h->dpad, 0, dbytes, st);
+    if (e == cudaSuccess) e = h->ops->adjoint(pts, npts, gout, h->lay32, h->dpad, st);
     if (e == cudaSuccess) {
-        const int4 n = make_int4(h->dims[0], h->dims[1], h->dims[2], h->dims[3]);
-        const int4 sd = make_int4(h->stride[0], h->stride[1], h->stride[2], h->stride[3]);
         const unsigned grid = (unsigned)std::min<int64_t>((h->coeff_count + 255) / 256, 148 * 32);
-        k_unpad_add<<<grid, 256, 0, st>>>(h->dpad, dcoeffs, h->coeff_count, h->s, n, sd, h->coset_elems,
-                                          2 * h->ops->halo);
+        k_unpad_add<<<grid, 256, 0, st>>>(h->dpad, dcoeffs, h->coeff_count, h->lay32);
         e = cudaPeekAtLastError();
     }
     if (e != cudaSuccess) cudaGetLastError();
@@ -472,8 +446,7 @@ interp_status interp_debug_indices(const interp_t *h, const float *pts, int64_t 
     if (!h || npts < 0) return INTERP_EINVAL;
     if (npts == 0) return INTERP_OK;
     if (!pts) return INTERP_EINVAL;
-    cudaError_t e = h->ops->debug(pts, npts, h->dims, h->stride, h->coset_elems, cells, piece,
-                                  static_cast<cudaStream_t>(stream));
+    cudaError_t e = h->ops->debug(pts, npts, h->lay32, cells, piece, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) cudaGetLastError();
     return cuda_status(e);
 }

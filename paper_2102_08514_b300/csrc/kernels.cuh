@@ -25,6 +25,7 @@
 #include <utility>
 
 #include "generated/splines.h"
+#include "layout.h"
 
 namespace ib {
 
@@ -187,11 +188,16 @@ constexpr uint64_t cosets_packed()
     return v;
 }
 
-// one slot of the folded offset: |y|, the signed stride of its original axis, and that axis
+// one slot of the folded offset: |y| and what the gather needs about the original axis it came
+// from (sign, within-brick coordinate of the cell, brick geometry of that axis)
 struct Slot {
     float y;
-    int ss;
-    int ax;
+    int sg;   // +1 / -1: sign of y along the original axis
+    int ax;   // original axis
+    int p;    // within-brick coordinate of the cell's padded index along that axis
+    int lb;   // log2 brick width of that axis
+    int bs;   // brick stride of that axis
+    int wt;   // within-brick weight of that axis
 };
 
 __device__ __forceinline__ void cswap(Slot &a, Slot &b)
@@ -227,54 +233,61 @@ constexpr uint64_t sigma_packed()
 // ------------------------------------------------------------------------------------ volume
 
 template <class CT> struct DevVol {
-    const CT *c;        // padded coset arrays, coset-major
-    int n[4];           // samples per axis of every coset (unpadded)
-    int stride[4];      // element strides of the padded layout
-    int coset_elems;    // elements of one padded coset array
+    const CT *c;        // padded, bricked coset arrays, coset-major
+    ibl::Layout L;
 };
 
-struct Fold {
-    int base;           // element offset of the nearest site (padded layout, coset included)
-    float t[4];         // folded offset y' (before the anchor shift)
-    int ss[4];          // signed stride of each folded slot
-    int ax[4];          // original axis of each folded slot
+template <int S> struct Fold {
+    int base;           // element offset of the brick holding the cell's site (coset included)
+    float t[S];         // folded offset y' (before the anchor shift)
+    Slot sl[S];         // per folded slot: sign, original axis and brick geometry
     int piece;
     bool in_range;
 };
 
+// element offset, relative to Fold::base, of the site displaced by o along folded slot A
+__device__ __forceinline__ int slot_term(const Slot &sl, int o)
+{
+    const int v = sl.p + sl.sg * o;
+    return (v >> sl.lb) * sl.bs + (v & ((1 << sl.lb) - 1)) * sl.wt;
+}
+
 // steps 1-3 for coset K of spline SP (K < 0: the run-time coset index kr)
 template <class SP, int K, class CT>
-__device__ __forceinline__ Fold fold_coset(const float (&x)[SP::S], const DevVol<CT> &v, int kr = 0)
+__device__ __forceinline__ Fold<SP::S> fold_coset(const float (&x)[SP::S], const DevVol<CT> &v, int kr = 0)
 {
     constexpr int S = SP::S;
     constexpr int H = SP::HALO;
-    Fold f;
-    int idx[S];
-    Slot sl[S];
+    constexpr int ESZ = (int)sizeof(CT);
+    Fold<S> f;
     bool ok = true;
-    int base = (K >= 0 ? K : kr) * v.coset_elems;
+    int base = (K >= 0 ? K : kr) * v.L.coset_elems;
     sfor<S>([&](auto A) {
         constexpr int a = decltype(A)::value;
+        constexpr int lb = ibl::brick_lb(S, ESZ, a);
+        int idx;
         float y;
         if constexpr (K >= 0) {
-            reduce_axis<SP::D, SP::COSET[K][a]>(x[a], idx[a], y);
+            reduce_axis<SP::D, SP::COSET[K][a]>(x[a], idx, y);
         } else {
             constexpr uint64_t packed = cosets_packed<SP>();
             const int l = (int)((packed >> (4 * (kr * S + a))) & 15u);
-            reduce_axis_rt<SP::D>(x[a], l, idx[a], y);
+            reduce_axis_rt<SP::D>(x[a], l, idx, y);
         }
-        ok &= (unsigned)(idx[a] + H) < (unsigned)(v.n[a] + 2 * H);
-        base += (idx[a] + 2 * H) * v.stride[a];
-        sl[a].y = fabsf(y);
-        sl[a].ss = (y < 0.0f) ? -v.stride[a] : v.stride[a];
-        sl[a].ax = a;
+        ok &= (unsigned)(idx + H) < (unsigned)(v.L.n[a] + 2 * H);
+        const int P = idx + 2 * H;                       // padded index of the cell's site
+        base += (P >> lb) * v.L.bstride[a];
+        Slot &sl = f.sl[a];
+        sl.y = fabsf(y);
+        sl.sg = (y < 0.0f) ? -1 : 1;
+        sl.ax = a;
+        sl.p = P & ((1 << lb) - 1);
+        sl.lb = lb;
+        sl.bs = v.L.bstride[a];
+        sl.wt = v.L.wt[a];
     });
-    sort_desc<S>(sl);
-    sfor<S>([&](auto A) {
-        f.t[A] = sl[A].y;
-        f.ss[A] = sl[A].ss;
-        f.ax[A] = sl[A].ax;
-    });
+    sort_desc<S>(f.sl);
+    sfor<S>([&](auto A) { f.t[A] = f.sl[A].y; });
     int j = 0;
     if constexpr (SP::K > 1) {
         unsigned q = 0;
@@ -297,24 +310,28 @@ __device__ __forceinline__ Fold fold_coset(const float (&x)[SP::S], const DevVol
     return f;
 }
 
+// element offset (relative to Fold::base) of stencil site M of piece J
+template <class SP, int J, int M>
+__device__ __forceinline__ int site_offset(const Fold<SP::S> &f)
+{
+    int off = 0;
+    sfor<SP::S>([&](auto A) {
+        constexpr int g = SP::SITE[J][M][decltype(A)::value];
+        off += slot_term(f.sl[A], g);
+    });
+    return off;
+}
+
 // steps 4-5 for piece J: accumulate f (and grad f if GRAD) into the query's sums
 template <class SP, int J, bool GRAD, class CT>
-__device__ __forceinline__ void eval_piece(const Fold &f, const DevVol<CT> &v, float &val, float (&grad)[SP::S])
+__device__ __forceinline__ void eval_piece(const Fold<SP::S> &f, const DevVol<CT> &v, float &val, float (&grad)[SP::S])
 {
     constexpr int S = SP::S;
     constexpr int NS = SP::NS[J];
     constexpr int NM = SP::NMON;
     const CT *cb = v.c + f.base;
     float c[NS];
-    sfor<NS>([&](auto Mi) {
-        constexpr int m = decltype(Mi)::value;
-        int off = 0;
-        sfor<S>([&](auto A) {
-            constexpr int g = SP::SITE[J][m][decltype(A)::value];
-            if constexpr (g != 0) off += g * f.ss[A];
-        });
-        c[m] = load_coef<CT>(cb + off);
-    });
+    sfor<NS>([&](auto Mi) { c[Mi] = load_coef<CT>(cb + site_offset<SP, J, decltype(Mi)::value>(f)); });
     float t[S];
     sfor<S>([&](auto A) {
         constexpr float an = SP::ANCHOR[J][decltype(A)::value];
@@ -330,8 +347,8 @@ __device__ __forceinline__ void eval_piece(const Fold &f, const DevVol<CT> &v, f
         val += r.v;
         // back through the fold: d/dx_ax = sign * d/dy'_slot
         sfor<S>([&](auto A) {
-            const float gs = (f.ss[A] < 0) ? -r.g[A] : r.g[A];
-            sfor<S>([&](auto B) { grad[B] += (f.ax[A] == B) ? gs : 0.0f; });
+            const float gs = (f.sl[A].sg < 0) ? -r.g[A] : r.g[A];
+            sfor<S>([&](auto B) { grad[B] += (f.sl[A].ax == B) ? gs : 0.0f; });
         });
     }
 }
@@ -343,14 +360,14 @@ __device__ __forceinline__ void eval_point(const float (&x)[SP::S], const DevVol
     if constexpr (SP::K == 1) {
         // one piece: unroll the coset loop (coset shifts become immediates)
         sfor<SP::M>([&](auto Kc) {
-            const Fold f = fold_coset<SP, decltype(Kc)::value, CT>(x, v);
+            const auto f = fold_coset<SP, decltype(Kc)::value, CT>(x, v);
             if (f.in_range) eval_piece<SP, 0, GRAD, CT>(f, v, val, grad);
         });
     } else {
         // several pieces: one copy of each piece's code, run-time coset loop
 #pragma unroll 1
         for (int k = 0; k < SP::M; ++k) {
-            const Fold f = fold_coset<SP, -1, CT>(x, v, k);
+            const auto f = fold_coset<SP, -1, CT>(x, v, k);
             if (f.in_range) {
                 sfor<SP::K>([&](auto Jc) {
                     if (f.piece == decltype(Jc)::value) eval_piece<SP, decltype(Jc)::value, GRAD, CT>(f, v, val, grad);
@@ -399,22 +416,15 @@ __global__ void __launch_bounds__(128) k_eval(const float *__restrict__ pts, int
 
 // w_site = sum_mon A[mon][site] mu[mon]; at the last nonzero of a site, scatter it
 template <class SP, int J, int NM, int SITE, int MON, float VAL, int FIRST, int SF, int SL>
-__device__ __forceinline__ void nz_scatter(const float (&mu)[NM], float &acc, const Fold &f, float *db,
+__device__ __forceinline__ void nz_scatter(const float (&mu)[NM], float &acc, const Fold<SP::S> &f, float *db,
                                            interp_gen::nz<SITE, MON, VAL, FIRST, SF, SL>)
 {
     if constexpr (SF) acc = mu[MON] * VAL;
     else acc = fmaf(mu[MON], VAL, acc);
-    if constexpr (SL) {
-        int off = 0;
-        sfor<SP::S>([&](auto A) {
-            constexpr int g = SP::SITE[J][SITE][decltype(A)::value];
-            if constexpr (g != 0) off += g * f.ss[A];
-        });
-        atomicAdd(db + off, acc);
-    }
+    if constexpr (SL) atomicAdd(db + site_offset<SP, J, SITE>(f), acc);
 }
 template <class SP, int J, int NM, class... Z>
-__device__ __forceinline__ void scatter_all(const float (&mu)[NM], const Fold &f, float *db, interp_gen::nzlist<Z...>)
+__device__ __forceinline__ void scatter_all(const float (&mu)[NM], const Fold<SP::S> &f, float *db, interp_gen::nzlist<Z...>)
 {
     float acc = 0.0f;
     (nz_scatter<SP, J, NM>(mu, acc, f, db, Z{}), ...);
@@ -422,7 +432,7 @@ __device__ __forceinline__ void scatter_all(const float (&mu)[NM], const Fold &f
 
 // dpad[site] += gout * phi(x - site) for every stencil site of piece J (padded FP32 layout)
 template <class SP, int J>
-__device__ __forceinline__ void adjoint_piece(const Fold &f, float *__restrict__ dpad, float w)
+__device__ __forceinline__ void adjoint_piece(const Fold<SP::S> &f, float *__restrict__ dpad, float w)
 {
     constexpr int S = SP::S;
     constexpr int NM = SP::NMON;
@@ -454,13 +464,13 @@ __global__ void __launch_bounds__(128) k_adjoint(const float *__restrict__ pts, 
     if (!finite || w == 0.0f) return;
     if constexpr (SP::K == 1) {
         sfor<SP::M>([&](auto Kc) {
-            const Fold f = fold_coset<SP, decltype(Kc)::value, float>(x, v);
+            const auto f = fold_coset<SP, decltype(Kc)::value, float>(x, v);
             if (f.in_range) adjoint_piece<SP, 0>(f, dpad, w);
         });
     } else {
 #pragma unroll 1
         for (int k = 0; k < SP::M; ++k) {
-            const Fold f = fold_coset<SP, -1, float>(x, v, k);
+            const auto f = fold_coset<SP, -1, float>(x, v, k);
             if (f.in_range) {
                 sfor<SP::K>([&](auto Jc) {
                     if (f.piece == decltype(Jc)::value) adjoint_piece<SP, decltype(Jc)::value>(f, dpad, w);
@@ -493,7 +503,7 @@ __global__ void k_debug(const float *__restrict__ pts, int64_t n, DevVol<float> 
             });
         }
         if (piece) {
-            const Fold f = fold_coset<SP, K, float>(x, v);
+            const auto f = fold_coset<SP, K, float>(x, v);
             piece[q * SP::M + K] = f.piece;
         }
     });

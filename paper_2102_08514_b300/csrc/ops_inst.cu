@@ -20,39 +20,35 @@ constexpr int kTPB = 128;
 using SP = interp_gen::INTERP_SPLINE;
 
 template <class CT>
-ib::DevVol<CT> make_vol(const void *c, const int *n, const int *stride, int coset_elems)
+ib::DevVol<CT> make_vol(const void *c, const ibl::Layout &L)
 {
     ib::DevVol<CT> v;
     v.c = static_cast<const CT *>(c);
-    for (int a = 0; a < 4; ++a) {
-        v.n[a] = n[a];
-        v.stride[a] = stride[a];
-    }
-    v.coset_elems = coset_elems;
+    v.L = L;
     return v;
 }
 
 inline unsigned grid_for(int64_t n) { return (unsigned)((n + kTPB - 1) / kTPB); }
 
 template <class CT, int MODE>
-cudaError_t launch_eval(const float *pts, int64_t n, const void *c, const int *dims, const int *stride, int ce,
-                        float *out, float *grad, const float *gout, cudaStream_t st)
+cudaError_t launch_eval(const float *pts, int64_t n, const void *c, const ibl::Layout &L, float *out, float *grad,
+                        const float *gout, cudaStream_t st)
 {
-    ib::k_eval<SP, CT, MODE><<<grid_for(n), kTPB, 0, st>>>(pts, n, make_vol<CT>(c, dims, stride, ce), out, grad, gout);
+    ib::k_eval<SP, CT, MODE><<<grid_for(n), kTPB, 0, st>>>(pts, n, make_vol<CT>(c, L), out, grad, gout);
     return cudaPeekAtLastError();
 }
 
-[[maybe_unused]] cudaError_t launch_adjoint(const float *pts, int64_t n, const float *gout, const int *dims,
-                                            const int *stride, int ce, float *dpad, cudaStream_t st)
+[[maybe_unused]] cudaError_t launch_adjoint(const float *pts, int64_t n, const float *gout, const ibl::Layout &L,
+                                            float *dpad, cudaStream_t st)
 {
-    ib::k_adjoint<SP><<<grid_for(n), kTPB, 0, st>>>(pts, n, gout, make_vol<float>(nullptr, dims, stride, ce), dpad);
+    ib::k_adjoint<SP><<<grid_for(n), kTPB, 0, st>>>(pts, n, gout, make_vol<float>(nullptr, L), dpad);
     return cudaPeekAtLastError();
 }
 
-[[maybe_unused]] cudaError_t launch_debug(const float *pts, int64_t n, const int *dims, const int *stride, int ce,
-                                          int32_t *cells, int32_t *piece, cudaStream_t st)
+[[maybe_unused]] cudaError_t launch_debug(const float *pts, int64_t n, const ibl::Layout &L, int32_t *cells,
+                                          int32_t *piece, cudaStream_t st)
 {
-    ib::k_debug<SP><<<grid_for(n), kTPB, 0, st>>>(pts, n, make_vol<float>(nullptr, dims, stride, ce), cells, piece);
+    ib::k_debug<SP><<<grid_for(n), kTPB, 0, st>>>(pts, n, make_vol<float>(nullptr, L), cells, piece);
     return cudaPeekAtLastError();
 }
 

@@ -5,14 +5,14 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "layout.h"
+
 namespace ibr {
 
-using EvalFn = cudaError_t (*)(const float *, int64_t, const void *, const int *, const int *, int, float *, float *,
+using EvalFn = cudaError_t (*)(const float *, int64_t, const void *, const ibl::Layout &, float *, float *,
                                const float *, cudaStream_t);
-using AdjFn = cudaError_t (*)(const float *, int64_t, const float *, const int *, const int *, int, float *,
-                              cudaStream_t);
-using DbgFn = cudaError_t (*)(const float *, int64_t, const int *, const int *, int, int32_t *, int32_t *,
-                              cudaStream_t);
+using AdjFn = cudaError_t (*)(const float *, int64_t, const float *, const ibl::Layout &, float *, cudaStream_t);
+using DbgFn = cudaError_t (*)(const float *, int64_t, const ibl::Layout &, int32_t *, int32_t *, cudaStream_t);
 
 struct SplineOps {
     const char *name = nullptr;

@@ -406,8 +406,18 @@ def analyse(name, L, xi, anchor_den=64, verbose=False):
             if all(abs(sum(p[a] * w[a] for a in range(s))) < halfw[p] for p in normals):
                 sites.append(list(g))
         polys = _piece_polynomials(cols, s, det_l, centre, D, z, sites)
-        anchor = [Fr(round(z[a] * anchor_den), anchor_den) for a in range(s)]
-        polys = [P.taylor_shift(anchor) for P in polys]
+        # expansion point: among the cell's vertices and its (dyadic-rounded) centroid, the one
+        # that leaves the fewest nonzero coefficients (fewest FMAs), then the smallest ones
+        cands = [list(v) for v in c.verts] + [[Fr(round(z[a] * anchor_den), anchor_den) for a in range(s)]]
+        best = None
+        for cand in cands:
+            if any((2 * anchor_den * v).denominator != 1 for v in cand):
+                continue                  # keep anchors exact in FP32
+            shifted = [P.taylor_shift(cand) for P in polys]
+            key = (sum(len(P.c) for P in shifted), max(abs(v) for P in shifted for v in P.c.values()))
+            if best is None or key < best[0]:
+                best = (key, cand, shifted)
+        _, anchor, polys = best
         code = sum((c.signs[i] << i) for i in range(len(planes)))
         pieces.append(Piece(anchor, sites, polys, code, c.verts, c.ineqs))
 
