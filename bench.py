@@ -115,6 +115,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the last ncu capture (profiles/traffic.txt), or None when the
+    library sources changed since that capture."""
+    from paper_2102_08514_b300 import build as b
+    digest = b.source_digest()[:16]
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.txt")) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) == 3 and parts[0] == kernel and parts[1] == digest:
+                    return int(parts[2])
+    except OSError:
+        pass
+    return None
+
+
 # ----------------------------------------------------------------------------- our arm
 
 def time_steps(torch, fn, steps, warmup, stream, barrier):
@@ -218,11 +234,7 @@ def run_ours(args):
     kern_ms = statistics.mean(per)
     achieved = flops_per_launch / (kern_ms * 1e-3) / 1e12
     peak = fp32_peak_tflops()
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "dram_traffic.json")
-    if os.path.exists(prof):
-        with open(prof) as f:
-            traffic = json.load(f).get(f"k_eval<{wl.spline},f32,grad>")
+    traffic = recorded_traffic(f"k_eval<{wl.spline},f32,grad>")
     line = {
         "metric": METRIC,
         "value": value,
