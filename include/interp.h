@@ -133,6 +133,28 @@ interp_status interp_backward(interp_t *h, const float *pts, int64_t npts, const
                               float *dpts, void *stream);
 
 /*
+ * interp_backward_noalloc -- the same adjoint as interp_backward, for callers that cannot call
+ * cudaMalloc when they run it: plug-ins whose host application owns the device allocator, loops
+ * with a fixed device-memory budget, and code paths where an allocation's implicit device
+ * synchronisation is not acceptable.  The paper has no counterpart; it is a deployment variant.  It allocates nothing: its padded FP32 gradient scratch
+ * is a static device array of INTERP_NOALLOC_MAX_GRAD_ELEMS floats (32 MiB) that every GPU which
+ * loads this library holds until the process exits.  The caller still passes all inputs and
+ * outputs (same arguments and semantics as interp_backward).
+ *
+ *   - Limit: n_cosets * (elements of one padded FP32 coset array) must not exceed
+ *     INTERP_NOALLOC_MAX_GRAD_ELEMS, else INTERP_ESIZE is returned and nothing runs.
+ *   - The first call on a device (with that device current, which must be the handle's device)
+ *     looks up the array's device address once; make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the previous call's contents; each call clears
+ *     the part it uses first.  Calls that overlap on the GPU (other streams, other threads) race
+ *     on it: serialise them.
+ * Errors: EINVAL, ESIZE, ECUDA.
+ */
+#define INTERP_NOALLOC_MAX_GRAD_ELEMS 8388608
+interp_status interp_backward_noalloc(interp_t *h, const float *pts, int64_t npts, const float *gout,
+                                      float *dcoeffs, float *dpts, void *stream);
+
+/*
  * interp_debug_indices -- for every query q and coset k: cells[(q*M + k)*s + a] = the index i of
  * the nearest coset site (the exact shift rho of Sec. 4.1 to the cube [-D/2, D/2)^s), and
  * piece[q*M + k] = the sub-region index j (Sec. 4.2) of the folded offset.  Either pointer may

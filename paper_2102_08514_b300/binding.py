@@ -63,8 +63,9 @@ def load(path: str = LIB_PATH):
     lib.interp_eval_grad.argtypes = [P, P, I64, P, P, P]
     lib.interp_backward.argtypes = [P, P, I64, P, P, P, P]
     lib.interp_debug_indices.argtypes = [P, P, I64, P, P, P]
+    lib.interp_backward_noalloc.argtypes = [P, P, I64, P, P, P, P]
     for f in (lib.interp_create, lib.interp_info, lib.interp_set_coeffs, lib.interp_eval, lib.interp_eval_grad,
-              lib.interp_backward, lib.interp_debug_indices):
+              lib.interp_backward, lib.interp_debug_indices, lib.interp_backward_noalloc):
         f.restype = I
     _lib = lib
     return lib
@@ -73,7 +74,7 @@ def load(path: str = LIB_PATH):
 def exported_symbols() -> list[str]:
     return ["interp_strerror", "interp_num_splines", "interp_spline_name", "interp_table_digest",
             "interp_create", "interp_destroy", "interp_info", "interp_set_coeffs", "interp_eval",
-            "interp_eval_grad", "interp_backward", "interp_debug_indices"]
+            "interp_eval_grad", "interp_backward", "interp_debug_indices", "interp_backward_noalloc"]
 
 
 def _strerror(st: int) -> str:
@@ -171,6 +172,17 @@ def interp_backward(h, pts, gout, dcoeffs, dpts=None, stream=None):
     _check(load().interp_backward(h, _dptr(pts, "pts", torch.float32), pts.shape[0],
                                   _dptr(gout, "gout", torch.float32), _dptr(dcoeffs, "dcoeffs", torch.float32),
                                   _dptr(dpts, "dpts", torch.float32), _stream(stream)), "interp_backward")
+
+
+def interp_backward_noalloc(h, pts, gout, dcoeffs, dpts=None, stream=None):
+    """The adjoint without any device allocation (scratch in a static device array); see the C
+    header for its size limit and the rule that overlapping calls race."""
+    import torch
+    _check(load().interp_backward_noalloc(h, _dptr(pts, "pts", torch.float32), pts.shape[0],
+                                          _dptr(gout, "gout", torch.float32),
+                                          _dptr(dcoeffs, "dcoeffs", torch.float32),
+                                          _dptr(dpts, "dpts", torch.float32), _stream(stream)),
+           "interp_backward_noalloc")
 
 
 def interp_debug_indices(h, pts, cells=None, piece=None, stream=None):

@@ -9,6 +9,7 @@
 #include <array>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -200,6 +201,35 @@ interp_status cuda_status(cudaError_t e)
 }  // namespace
 
 // ------------------------------------------------------------------------------------ the handle
+
+// Gradient scratch of interp_backward_noalloc: a file-scope device array, so that entry point
+// allocates nothing.  Host code must not use the name as a pointer: the device address comes from
+// cudaGetSymbolAddress, looked up once per device and cached below.
+static __device__ __align__(256) float g_noalloc_scratch[INTERP_NOALLOC_MAX_GRAD_ELEMS];
+
+namespace {
+constexpr int kMaxDevices = 128;
+std::mutex g_noalloc_mu;
+float *g_noalloc_ptr[kMaxDevices] = {};
+
+// device address of g_noalloc_scratch on the current device (set up on the first call there)
+interp_status noalloc_scratch(int dev, float **out)
+{
+    if (dev < 0 || dev >= kMaxDevices) return INTERP_EINVAL;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        float *ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress((void **)&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            return INTERP_ECUDA;
+        }
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = g_noalloc_ptr[dev];
+    return INTERP_OK;
+}
+}  // namespace
 
 struct interp {
     const SplineOps *ops = nullptr;
@@ -434,6 +464,41 @@ interp_status interp_backward(interp_t *h, const float *pts, int64_t npts, const
     if (e == cudaSuccess) {
         const unsigned grid = (unsigned)std::min<int64_t>((h->coeff_count + 255) / 256, 148 * 32);
         k_unpad_add<<<grid, 256, 0, st>>>(h->dpad, dcoeffs, h->coeff_count, h->lay32);
+        e = cudaPeekAtLastError();
+    }
+    if (e != cudaSuccess) cudaGetLastError();
+    return cuda_status(e);
+}
+
+interp_status interp_backward_noalloc(interp_t *h, const float *pts, int64_t npts, const float *gout, float *dcoeffs,
+                                      float *dpts, void *stream)
+{
+    if (!h || npts < 0) return INTERP_EINVAL;
+    const int64_t need = (int64_t)h->lay32.coset_elems * h->ops->M;
+    if (need > INTERP_NOALLOC_MAX_GRAD_ELEMS) return INTERP_ESIZE;
+    if (npts == 0) return INTERP_OK;
+    if (!pts || !gout) return INTERP_EINVAL;
+    if (npts > (int64_t)INT32_MAX * kTPB) return INTERP_ESIZE;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return INTERP_ECUDA;
+    }
+    if (dev != h->device) return INTERP_EINVAL;
+    if (dpts) {
+        interp_status s2 = eval_common(h, pts, npts, nullptr, dpts, gout, 2, stream);
+        if (s2 != INTERP_OK) return s2;
+    }
+    if (!dcoeffs) return INTERP_OK;
+    float *scratch = nullptr;
+    interp_status st0 = noalloc_scratch(dev, &scratch);
+    if (st0 != INTERP_OK) return st0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(scratch, 0, (size_t)need * sizeof(float), st);
+    if (e == cudaSuccess) e = h->ops->adjoint(pts, npts, gout, h->lay32, scratch, st);
+    if (e == cudaSuccess) {
+        const unsigned grid = (unsigned)std::min<int64_t>((h->coeff_count + 255) / 256, 148 * 32);
+        k_unpad_add<<<grid, 256, 0, st>>>(scratch, dcoeffs, h->coeff_count, h->lay32);
         e = cudaPeekAtLastError();
     }
     if (e != cudaSuccess) cudaGetLastError();
