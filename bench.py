@@ -36,6 +36,9 @@ from synth import LATTICES, SPLINES, WORKLOADS, coefficients, interior_box, make
 
 WORKLOAD = "bcc_quintic_128"
 METRIC = "evals/s (value+grad, FP32, <=2e-6 rel err)"
+# default timed form per workload (the headline is bcc_quintic_128: value + gradient)
+DEFAULT_FORM = {"bcc_linear_16": "value", "bcc_quintic_128": "value_grad", "fcc_6dir_128": "value_grad",
+                "cc_7dir_256": "value", "d4s_8dir_48": "value"}
 UNIT = "evals/s"
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
@@ -55,10 +58,16 @@ def fp32_peak_tflops():
     return SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 
-def workload_description(wl):
-    return (f"{wl.name}: BCC quintic box spline (8 directions), 2 x {wl.dims[0]}^3 FP32 coefficients "
-            f"sampled from the Marschner-Lobb signal, {wl.queries} uniform random queries in the lattice "
-            f"interior, value + gradient")
+def workload_description(wl, form="value_grad", storage="f32"):
+    sp = SPLINES[wl.spline]
+    lat = LATTICES[sp.lattice]
+    what = {"value": "value", "value_grad": "value + gradient", "adjoint": "adjoint (dL/dc)"}[form]
+    src = {"signal": "sampled from the Marschner-Lobb signal", "uniform": "uniform in [-1,1]",
+           "normal": "standard normal"}[wl.coeffs]
+    shape = " x ".join(str(d) for d in wl.dims)
+    return (f"{wl.name}: {wl.spline} box spline ({np.asarray(sp.xi).shape[1]} directions) on {lat.name.upper()}, "
+            f"{len(lat.cosets)} x {shape} {storage.upper()} coefficients {src}, {wl.queries} uniform random "
+            f"queries in the lattice interior, {what}")
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -155,6 +164,103 @@ def time_steps(torch, fn, steps, warmup, stream, barrier):
     return t0.elapsed_time(t1), per
 
 
+def run_batch(args):
+    """Batched workload: 64 volumes of uneven size and mixed lattice / spline (2^20 queries each)
+    plus the D4* volume (2^24 queries), one graph-replayed persistent launch per step."""
+    import torch
+    from paper_2102_08514_b300.binding import Batch, Interpolator
+    from synth import batch_volumes
+
+    items = []
+    total_q = 0
+    flops = 0.0
+    vols = batch_volumes(64) + [("d4s_8dir", (48, 48, 48, 48))]
+    for v, (name, dims) in enumerate(vols):
+        sp = SPLINES[name]
+        lat = LATTICES[sp.lattice]
+        itp = Interpolator(np.asarray(lat.L), np.asarray(sp.xi), dims, "f32")
+        rng = make_rng(2106, v)
+        itp.set_coeffs(torch.from_numpy(rng.uniform(-1, 1, itp.shape).astype(np.float32)).cuda())
+        nq = (1 << 24) if name == "d4s_8dir" else (1 << 20)
+        if args.queries:
+            nq = min(nq, args.queries)
+        lo, hi = interior_box(name, dims)
+        pts = torch.from_numpy(uniform_points(rng, nq, lo, hi)).cuda()
+        out = torch.empty(nq, device="cuda")
+        items.append((itp, pts, out))
+        total_q += nq
+        flops += 2.0 * itp.info.fma_value_per_query * nq
+    batch = Batch(items)
+    tiles = batch.autotune()
+    stream = torch.cuda.current_stream()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        total_ms, per = time_steps(torch, batch.run, args.steps, args.warmup, stream, lambda: None)
+    ms = total_ms / args.steps
+    achieved = flops / (ms * 1e-3) / 1e12
+    peak = fp32_peak_tflops()
+    line = {
+        "metric": "evals/s (batched value, FP32)", "value": total_q / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded; uniform)",
+        "config": {"workload": f"batch64: 64 volumes (edge lengths log-uniform in 32..256, splines bcc_linear / "
+                               f"bcc_quintic / fcc_6dir / cc_7dir in turn) x 2^20 queries + d4s_8dir 2 x 48^4 x "
+                               f"2^24 queries, one persistent launch per dimension replayed from a CUDA graph",
+                   "queries": total_q, "tiles": tiles},
+        "gpu_launches": 2 * args.steps, "clocks": clk.summary(),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_batch (3-D and 4-D)"},
+    }
+    print(json.dumps(line), flush=True)
+
+
+RAY_EVALS = [0]
+
+
+def time_rays(torch, itp, wl, steps, warmup, stream, barrier):
+    """1024 x 1024 orthographic rays x 256 steps through the interior box (value, value + grad)."""
+    from paper_2102_08514_b300.binding import interp_eval_rays, make_rays
+    from synth import ray_points, ray_setup
+    W = H = 1024
+    S = 256
+    setup = ray_setup(wl.spline, wl.dims, W, H, S)
+    eu, ev = setup["eu"], setup["ev"]
+    origin = setup["centre"] - setup["half_u"] * eu - setup["half_v"] * ev
+    rays = make_rays(origin, (2.0 * setup["half_u"] / W) * eu, (2.0 * setup["half_v"] / H) * ev, setup["d"],
+                     setup["lo"], setup["hi"], W, H, S)
+    pix = np.stack(np.meshgrid(np.arange(W), np.arange(H), indexing="xy"), -1).reshape(-1, 2)
+    _, valid = ray_points(setup, pix)
+    RAY_EVALS[0] = int(valid.sum()) * S
+    out1 = torch.empty(W * H, device="cuda")
+    out4 = torch.empty(W * H * 4, device="cuda")
+    res = {}
+    _, per = time_steps(torch, lambda: interp_eval_rays(itp.handle, rays, out1), steps, warmup, stream, barrier)
+    res["rays_value"] = statistics.mean(per)
+    _, per = time_steps(torch, lambda: interp_eval_rays(itp.handle, rays, out4, with_grad=True), steps, warmup,
+                        stream, barrier)
+    res["rays_value_grad"] = statistics.mean(per)
+    return res
+
+
+def time_fit_step(torch, itp, wl, pts, pts_h, steps, warmup, stream, barrier):
+    """One Adam step of the coefficient fit: set coefficients, evaluate, FP64 loss, adjoint, update."""
+    from paper_2102_08514_b300.fit import mse_loss
+    from paper_2102_08514_b300.binding import lattice_interp
+    from synth import marschner_lobb
+    lat = LATTICES[SPLINES[wl.spline].lattice]
+    phys = -1.0 + pts_h.astype(np.float64) / (lat.D * np.asarray(wl.dims) / 2.0)
+    y = torch.from_numpy(marschner_lobb(phys).astype(np.float32)).cuda()
+    c = torch.zeros(itp.shape, device="cuda", requires_grad=True)
+    opt = torch.optim.Adam([c], lr=0.05)
+
+    def step():
+        opt.zero_grad(set_to_none=False)
+        mse_loss(lattice_interp(pts, c, itp), y).backward()
+        opt.step()
+
+    _, per = time_steps(torch, step, steps, warmup, stream, barrier)
+    return statistics.mean(per)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -179,25 +285,29 @@ def run_ours(args):
 
     from paper_2102_08514_b300.binding import Interpolator
 
-    wl = WORKLOADS[WORKLOAD]
+    wl = WORKLOADS[args.workload]
+    form = args.form or DEFAULT_FORM[wl.name]
     sp = SPLINES[wl.spline]
     lat = LATTICES[sp.lattice]
-    itp = Interpolator(np.asarray(lat.L), np.asarray(sp.xi), wl.dims, "f32")
+    itp = Interpolator(np.asarray(lat.L), np.asarray(sp.xi), wl.dims, args.storage)
+    s = itp.s
     c = coefficients(wl)
-    itp.set_coeffs(torch.from_numpy(c).cuda())
+    tdt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[args.storage]
+    itp.set_coeffs(torch.from_numpy(c).to(tdt).cuda())
     lo, hi = interior_box(wl.spline, wl.dims)
-    n = wl.queries
+    n = args.queries or wl.queries
     pts_h = uniform_points(make_rng(wl.seed + 1000 * rank, 0), n, lo, hi)
     pts = torch.from_numpy(pts_h).cuda()
     out = torch.empty(n, device="cuda")
-    grad = torch.empty(n, 3, device="cuda")
+    grad = torch.empty(n, s, device="cuda")
     gout = torch.from_numpy(make_rng(wl.seed, 5).uniform(-1, 1, n).astype(np.float32)).cuda()
     dcoef = torch.zeros(itp.shape, device="cuda")
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
-
-    def step():
-        itp.eval_grad(pts, out, grad)
+    run_form = {"value": lambda: itp.eval(pts, out),
+                "value_grad": lambda: itp.eval_grad(pts, out, grad),
+                "adjoint": lambda: itp.backward(pts, gout, dcoef)}
+    step = run_form[form]
 
     with ClockSampler(torch.cuda.current_device()) as clk:
         total_ms, per = time_steps(torch, step, args.steps, args.warmup, stream, barrier)
@@ -206,35 +316,61 @@ def run_ours(args):
     ms_step = total_ms / args.steps
     value = world * n / (ms_step * 1e-3)
 
-    # forms: plain FP32 value path and the adjoint, same timing rules
+    # every form, same timing rules (the timed step above is one of them)
     fw = max(args.warmup, 3)
-    fsteps = max(3, min(args.steps, 10))
-    _, per_v = time_steps(torch, lambda: itp.eval(pts, out), fsteps, fw, stream, barrier)
-    _, per_a = time_steps(torch, lambda: itp.backward(pts, gout, dcoef), fsteps, fw, stream, barrier)
-    ms_v = statistics.mean(per_v)
-    ms_a = statistics.mean(per_a)
+    fsteps = max(3, min(args.steps, 20))
+    form_ms = {}
+    for name_f, fn in run_form.items():
+        _, per_f = time_steps(torch, fn, fsteps, fw, stream, barrier)
+        form_ms[name_f] = statistics.mean(per_f)
 
-    # e2e: points from pinned host memory, eval_grad, results back to pinned host memory
+    # workload-specific forms: ray-coherent queries (bcc_quintic_128), one fitting step (fcc_6dir_128)
+    if wl.name == "bcc_quintic_128" and args.storage == "f32":
+        form_ms.update(time_rays(torch, itp, wl, fsteps, fw, stream, barrier))
+    if wl.name == "fcc_6dir_128" and args.storage == "f32":
+        form_ms["fit_step"] = time_fit_step(torch, itp, wl, pts, pts_h, fsteps, fw, stream, barrier)
+
+    # e2e: points from pinned host memory, the step, results back to pinned host memory
     pts_pin = torch.from_numpy(pts_h).pin_memory()
-    out_pin = torch.empty(n, pin_memory=True)
-    grad_pin = torch.empty(n, 3, pin_memory=True)
     pts_d = torch.empty_like(pts)
+    if form == "adjoint":
+        g_pin = gout.cpu().pin_memory()
+        g_d = torch.empty_like(gout)
+        dc_pin = torch.empty(itp.shape, pin_memory=True)
+        h2d, d2h = n * s * 4 + n * 4, dcoef.numel() * 4
 
-    def e2e_step():
-        pts_d.copy_(pts_pin, non_blocking=True)
-        itp.eval_grad(pts_d, out, grad)
-        out_pin.copy_(out, non_blocking=True)
-        grad_pin.copy_(grad, non_blocking=True)
+        def e2e_step():
+            pts_d.copy_(pts_pin, non_blocking=True)
+            g_d.copy_(g_pin, non_blocking=True)
+            dcoef.zero_()
+            itp.backward(pts_d, g_d, dcoef)
+            dc_pin.copy_(dcoef, non_blocking=True)
+    else:
+        out_pin = torch.empty(n, pin_memory=True)
+        grad_pin = torch.empty(n, s, pin_memory=True)
+        h2d, d2h = n * s * 4, n * 4 * (1 + (s if form == "value_grad" else 0))
 
-    e2e_ms, _ = time_steps(torch, e2e_step, max(3, min(args.steps, 10)), fw, stream, barrier)
-    e2e_ms = max_over_ranks(e2e_ms) / max(3, min(args.steps, 10))
+        def e2e_step():
+            pts_d.copy_(pts_pin, non_blocking=True)
+            if form == "value_grad":
+                itp.eval_grad(pts_d, out, grad)
+                grad_pin.copy_(grad, non_blocking=True)
+            else:
+                itp.eval(pts_d, out)
+            out_pin.copy_(out, non_blocking=True)
+
+    e2e_steps = max(3, min(args.steps, 10))
+    e2e_ms, _ = time_steps(torch, e2e_step, e2e_steps, fw, stream, barrier)
+    e2e_ms = max_over_ranks(e2e_ms) / e2e_steps
 
     info = itp.info
-    flops_per_launch = 2.0 * info.fma_grad_per_query * n
+    fma = info.fma_grad_per_query if form == "value_grad" else info.fma_value_per_query
+    flops_per_launch = 2.0 * fma * n
     kern_ms = statistics.mean(per)
     achieved = flops_per_launch / (kern_ms * 1e-3) / 1e12
     peak = fp32_peak_tflops()
-    traffic = recorded_traffic(f"k_eval<{wl.spline},f32,grad>")
+    kname = f"k_eval<{wl.spline},{args.storage},{form}>" if form != "adjoint" else f"k_adjoint<{wl.spline}>"
+    traffic = recorded_traffic(kname)
     line = {
         "metric": METRIC,
         "value": value,
@@ -247,28 +383,30 @@ def run_ours(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
-        "data": "synthetic (seeded; Marschner-Lobb samples, uniform random queries)",
-        "config": {"workload": workload_description(wl), "queries_per_gpu": n, "coeffs": list(itp.shape),
+        "data": "synthetic (seeded; " + ("Marschner-Lobb samples" if wl.coeffs == "signal" else wl.coeffs)
+                + ", uniform random queries)",
+        "config": {"workload": workload_description(wl, form, args.storage), "queries_per_gpu": n,
+                   "coeffs": list(itp.shape), "storage": args.storage,
                    "parallelism": f"replicas x{world} (independent queries)",
-                   "l2": "inputs larger than L2 (points 201 MB per GPU); coefficients (20 MB padded) stay L2-resident"},
-        "e2e": {"value": world * n / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": n * 3 * 4,
-                "d2h_bytes_per_step": n * 4 * 4},
+                   "l2": f"inputs larger than L2 (points {n * s * 4 / 1e6:.0f} MB per GPU)" if n * s * 4 > 126e6
+                   else f"inputs {n * s * 4 / 1e6:.0f} MB (smaller than L2)"},
+        "e2e": {"value": world * n / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
         "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": f"k_eval<{wl.spline},f32,value+grad>",
-                     "flops_per_query": 2.0 * info.fma_grad_per_query,
-                     "peak_note": "FP32 FMA peak derived: 148 SMs x 128 lanes x 2 FLOP x 2032 MHz"},
-        "forms": {
-            "value_grad": {"evals_per_s": n / (kern_ms * 1e-3), "ms": kern_ms},
-            "value": {"evals_per_s": n / (ms_v * 1e-3), "ms": ms_v,
-                      "tflops": 2.0 * info.fma_value_per_query * n / (ms_v * 1e-3) / 1e12},
-            "adjoint": {"evals_per_s": n / (ms_a * 1e-3), "ms": ms_a},
-        },
+                     "frac": achieved / peak, "traffic": traffic, "kernel": kname,
+                     "flops_per_query": 2.0 * fma,
+                     "peak_note": "FP32 FMA peak derived: 148 SMs x 128 lanes x 2 FLOP x 2032 MHz (of derived)"},
+        "forms": {k: {"evals_per_s": (RAY_EVALS[0] if k.startswith("rays") else n) / (v * 1e-3), "ms": v}
+                  for k, v in form_ms.items()},
     }
+    line["forms"]["value"]["tflops"] = 2.0 * info.fma_value_per_query * n / (form_ms["value"] * 1e-3) / 1e12
+    line["forms"]["value_grad"]["tflops"] = 2.0 * info.fma_grad_per_query * n / (form_ms["value_grad"] * 1e-3) / 1e12
+    if args.workload != WORKLOAD or args.storage != "f32" or form != DEFAULT_FORM[WORKLOAD]:
+        line["metric"] = f"evals/s ({form}, {args.storage} storage)"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, pts_h, c, seconds=args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(wl, pts_h, c, form, seconds=args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -286,7 +424,7 @@ def _oracle_setup(wl):
     return oracle, oracle.Spline(xi, detl), lat
 
 
-def cpu_baseline(wl, pts, c, seconds=15.0):
+def cpu_baseline(wl, pts, c, form="value_grad", seconds=15.0):
     """Time the FP64 oracle (as it stands) on the host cores on a bounded sample."""
     orc, spl, lat = _oracle_setup(wl)
     cores = os.cpu_count() or 1
@@ -296,21 +434,23 @@ def cpu_baseline(wl, pts, c, seconds=15.0):
     while True:
         sample = pts[off:off + m].astype(np.float64)
         t = time.perf_counter()
-        orc.eval_sum(spl, lat.D, lat.cosets, cd, sample, grad=True, nthreads=cores)
+        orc.eval_sum(spl, lat.D, lat.cosets, cd, sample, grad=(form != "value"), nthreads=cores)
         dt = time.perf_counter() - t
         off += m
         if dt >= 0.5 * seconds or off + 2 * m > len(pts):
             break
         m = int(min(len(pts) - off, m * max(2.0, min(8.0, seconds / max(dt, 1e-3)))))
     return {"value": m / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{m} of the {wl.queries} queries (value+grad, FP64, brute-force recurrence), {dt:.1f} s"}
+            "sample": f"{m} of the {wl.queries} queries ({'value' if form == 'value' else 'value+grad'}, FP64, "
+                      f"brute-force recurrence), {dt:.1f} s"}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl = WORKLOADS[WORKLOAD]
+    wl = WORKLOADS[args.workload]
+    form = args.form or DEFAULT_FORM[wl.name]
     orc, spl, lat = _oracle_setup(wl)
     cores = os.cpu_count() or 1
     c = coefficients(wl).astype(np.float64)
@@ -319,14 +459,17 @@ def run_reference(args):
     # size each step so the whole run takes a few minutes
     probe = pts[:cores * 2]
     t = time.perf_counter()
-    orc.eval_sum(spl, lat.D, lat.cosets, c, probe, grad=True, nthreads=cores)
+    orc.eval_sum(spl, lat.D, lat.cosets, c, probe, grad=(form != "value"), nthreads=cores)
     rate = len(probe) / max(time.perf_counter() - t, 1e-6)
     per_step = int(max(cores, min(len(pts) // (args.steps + args.warmup + 1), rate * 120.0 / (args.steps + args.warmup))))
     off = len(probe)
 
     def step(i):
         sl = pts[off + (i * per_step) % (len(pts) - off - per_step):][:per_step]
-        orc.eval_sum(spl, lat.D, lat.cosets, c, sl, grad=True, nthreads=cores)
+        if form == "adjoint":
+            orc.adjoint(spl, lat.D, lat.cosets, c.shape, sl, np.ones(len(sl)))
+        else:
+            orc.eval_sum(spl, lat.D, lat.cosets, c, sl, grad=(form != "value"), nthreads=cores)
 
     for i in range(args.warmup):
         step(i)
@@ -336,10 +479,11 @@ def run_reference(args):
     dt = time.perf_counter() - t
     value = per_step * args.steps / dt
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+        "impl": "reference", "metric": METRIC if args.workload == WORKLOAD and form == DEFAULT_FORM[WORKLOAD]
+        else f"evals/s ({form}, {args.storage} storage)", "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
-        "config": {"workload": workload_description(wl), "sample_per_step": per_step},
+        "config": {"workload": workload_description(wl, form, args.storage), "sample_per_step": per_step},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{per_step} queries per step of the {wl.queries}-query workload"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -355,11 +499,17 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch64"], default=WORKLOAD)
+    ap.add_argument("--form", choices=["value", "value_grad", "adjoint"], default=None)
+    ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
+    ap.add_argument("--queries", type=int, default=0, help="override the workload's query count")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch64":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -133,6 +133,40 @@ interp_status interp_backward(interp_t *h, const float *pts, int64_t npts, const
                               float *dpts, void *stream);
 
 /*
+ * Batched evaluation (not in the paper): interp_eval over many handles of mixed lattice and spline
+ * type in ONE persistent launch per dimension (3-D handles and 4-D handles), replayed from a CUDA
+ * graph.  Work items are (handle, tile of queries); resident CTAs claim them from a counter, so
+ * cheap and expensive splines balance across the GPU.  Every handle must use FP32 storage.
+ *
+ *   interp_batch_create    records the items (handles, point / output pointers, counts); the
+ *                          pointers must stay valid for the batch's lifetime.  Allocates the
+ *                          device descriptor table.  Errors: EINVAL, EUNSUPPORTED (16-bit
+ *                          storage), ENOMEM, ECUDA.
+ *   interp_batch_autotune  times the candidate tile sizes (256 .. 8192 queries) for each spline
+ *                          in the batch on `stream` (running the batch several times: outputs
+ *                          are overwritten) and keeps the fastest; blocks until done.
+ *   interp_batch_tile /    read / set the tile size of a spline by name (e.g. to re-apply a
+ *   interp_batch_set_tile  previous autotune result).  Tile sizes must be multiples of 128.
+ *   interp_batch_run       out_i[q] = f_i(pts_i[q]) for every item: launches the batch's CUDA
+ *                          graph (captured on the first run after create or a tile change) on
+ *                          `stream`.  Runs of one batch must not overlap each other.
+ *   interp_batch_destroy   releases it (NULL is a no-op).  Synchronises the device.
+ */
+typedef struct interp_batch interp_batch_t;
+typedef struct {
+    const interp_t *vol;   /* handle (FP32 storage)          */
+    const float *pts;      /* device, npts x s, row-major    */
+    int64_t npts;          /* >= 0                           */
+    float *out;            /* device, npts                   */
+} interp_batch_item;
+interp_status interp_batch_create(const interp_batch_item *items, int n, interp_batch_t **out);
+interp_status interp_batch_autotune(interp_batch_t *b, void *stream);
+interp_status interp_batch_tile(const interp_batch_t *b, const char *spline, int *tile);
+interp_status interp_batch_set_tile(interp_batch_t *b, const char *spline, int tile);
+interp_status interp_batch_run(interp_batch_t *b, void *stream);
+void interp_batch_destroy(interp_batch_t *b);
+
+/*
  * interp_backward_noalloc -- the same adjoint as interp_backward, for callers that cannot call
  * cudaMalloc when they run it: plug-ins whose host application owns the device allocator, loops
  * with a fixed device-memory budget, and code paths where an allocation's implicit device
@@ -153,6 +187,26 @@ interp_status interp_backward(interp_t *h, const float *pts, int64_t npts, const
 #define INTERP_NOALLOC_MAX_GRAD_ELEMS 8388608
 interp_status interp_backward_noalloc(interp_t *h, const float *pts, int64_t npts, const float *gout,
                                       float *dcoeffs, float *dpts, void *stream);
+
+/*
+ * interp_eval_rays -- ray-coherent queries (not in the paper; the paper's timings come from a
+ * volume renderer that marches rays through mostly transparent volumes, Sec. 5.1).  For every
+ * pixel (px, py) of a width x height image, the ray starts at
+ *     o = origin + (px + 1/2) du + (py + 1/2) dv
+ * and runs along dir (any length); its chord with the box [box_lo, box_hi] is split into `steps`
+ * equal steps sampled at their midpoints (rays that miss the box give 0).  Output per pixel
+ * (row-major, pixel = py * width + px):
+ *     with_grad = 0:  out[pixel]         = sum over samples of f
+ *     with_grad = 1:  out[4*pixel + 0]   = sum of f,  out[4*pixel + 1 + a] = sum of d f / d x_a
+ * pts_out (NULL or width*height*steps*3 floats) receives every sample point (NaN for missed rays).
+ * 3-D splines with FP32 storage only (else EUNSUPPORTED).  Errors: EINVAL, EUNSUPPORTED, ECUDA.
+ */
+typedef struct {
+    float origin[3], du[3], dv[3], dir[3], box_lo[3], box_hi[3];
+    int32_t width, height, steps;
+} interp_rays_t;
+interp_status interp_eval_rays(const interp_t *h, const interp_rays_t *rays, int with_grad, float *out,
+                               float *pts_out, void *stream);
 
 /*
  * interp_debug_indices -- for every query q and coset k: cells[(q*M + k)*s + a] = the index i of

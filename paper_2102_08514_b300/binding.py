@@ -39,6 +39,17 @@ class InterpInfo(ctypes.Structure):
                 ("name", ctypes.c_char_p)]
 
 
+class Rays(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_float * 3), ("du", ctypes.c_float * 3), ("dv", ctypes.c_float * 3),
+                ("dir", ctypes.c_float * 3), ("box_lo", ctypes.c_float * 3), ("box_hi", ctypes.c_float * 3),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("steps", ctypes.c_int32)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("vol", ctypes.c_void_p), ("pts", ctypes.c_void_p), ("npts", ctypes.c_int64),
+                ("out", ctypes.c_void_p)]
+
+
 def load(path: str = LIB_PATH):
     """Load libinterp_b300.so (raises if it has not been built)."""
     global _lib
@@ -64,6 +75,18 @@ def load(path: str = LIB_PATH):
     lib.interp_backward.argtypes = [P, P, I64, P, P, P, P]
     lib.interp_debug_indices.argtypes = [P, P, I64, P, P, P]
     lib.interp_backward_noalloc.argtypes = [P, P, I64, P, P, P, P]
+    lib.interp_eval_rays.argtypes = [P, ctypes.POINTER(Rays), I, P, P, P]
+    lib.interp_eval_rays.restype = I
+    lib.interp_batch_create.argtypes = [ctypes.POINTER(BatchItem), I, ctypes.POINTER(ctypes.c_void_p)]
+    lib.interp_batch_autotune.argtypes = [P, P]
+    lib.interp_batch_tile.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]
+    lib.interp_batch_set_tile.argtypes = [P, ctypes.c_char_p, I]
+    lib.interp_batch_run.argtypes = [P, P]
+    lib.interp_batch_destroy.argtypes = [P]
+    lib.interp_batch_destroy.restype = None
+    for f in (lib.interp_batch_create, lib.interp_batch_autotune, lib.interp_batch_tile, lib.interp_batch_set_tile,
+              lib.interp_batch_run):
+        f.restype = I
     for f in (lib.interp_create, lib.interp_info, lib.interp_set_coeffs, lib.interp_eval, lib.interp_eval_grad,
               lib.interp_backward, lib.interp_debug_indices, lib.interp_backward_noalloc):
         f.restype = I
@@ -74,7 +97,9 @@ def load(path: str = LIB_PATH):
 def exported_symbols() -> list[str]:
     return ["interp_strerror", "interp_num_splines", "interp_spline_name", "interp_table_digest",
             "interp_create", "interp_destroy", "interp_info", "interp_set_coeffs", "interp_eval",
-            "interp_eval_grad", "interp_backward", "interp_debug_indices", "interp_backward_noalloc"]
+            "interp_eval_grad", "interp_backward", "interp_debug_indices", "interp_backward_noalloc",
+            "interp_batch_create", "interp_batch_autotune", "interp_batch_tile", "interp_batch_set_tile",
+            "interp_batch_run", "interp_batch_destroy", "interp_eval_rays"]
 
 
 def _strerror(st: int) -> str:
@@ -190,6 +215,94 @@ def interp_debug_indices(h, pts, cells=None, piece=None, stream=None):
     _check(load().interp_debug_indices(h, _dptr(pts, "pts", torch.float32), pts.shape[0],
                                        _dptr(cells, "cells", torch.int32), _dptr(piece, "piece", torch.int32),
                                        _stream(stream)), "interp_debug_indices")
+
+
+def make_rays(origin, du, dv, direction, box_lo, box_hi, width, height, steps) -> Rays:
+    r = Rays()
+    for name, v in (("origin", origin), ("du", du), ("dv", dv), ("dir", direction), ("box_lo", box_lo),
+                    ("box_hi", box_hi)):
+        getattr(r, name)[:] = [float(a) for a in v]
+    r.width, r.height, r.steps = int(width), int(height), int(steps)
+    return r
+
+
+def interp_eval_rays(h, rays: Rays, out, with_grad: bool = False, pts_out=None, stream=None):
+    """Per-pixel sums of f (and grad f) along orthographic rays; see the C header."""
+    import torch
+    _check(load().interp_eval_rays(h, ctypes.byref(rays), int(with_grad), _dptr(out, "out", torch.float32),
+                                   _dptr(pts_out, "pts_out", torch.float32), _stream(stream)), "interp_eval_rays")
+
+
+def interp_batch_create(items):
+    """items: list of (handle, pts tensor, out tensor).  The tensors must outlive the batch."""
+    import torch
+    arr = (BatchItem * len(items))()
+    for i, (h, pts, out) in enumerate(items):
+        arr[i].vol = h.value if isinstance(h, ctypes.c_void_p) else h
+        arr[i].pts = _dptr(pts, "pts", torch.float32).value if pts.numel() else None
+        arr[i].npts = pts.shape[0]
+        arr[i].out = _dptr(out, "out", torch.float32).value if out.numel() else None
+    b = ctypes.c_void_p()
+    _check(load().interp_batch_create(arr, len(items), ctypes.byref(b)), "interp_batch_create")
+    return b
+
+
+def interp_batch_autotune(b, stream=None):
+    _check(load().interp_batch_autotune(b, _stream(stream)), "interp_batch_autotune")
+
+
+def interp_batch_tile(b, spline: str) -> int:
+    t = ctypes.c_int()
+    _check(load().interp_batch_tile(b, spline.encode(), ctypes.byref(t)), "interp_batch_tile")
+    return t.value
+
+
+def interp_batch_set_tile(b, spline: str, tile: int):
+    _check(load().interp_batch_set_tile(b, spline.encode(), tile), "interp_batch_set_tile")
+
+
+def interp_batch_run(b, stream=None):
+    _check(load().interp_batch_run(b, _stream(stream)), "interp_batch_run")
+
+
+def interp_batch_destroy(b):
+    if b:
+        load().interp_batch_destroy(b)
+
+
+class Batch:
+    """Many (Interpolator, points, output) triples evaluated by one persistent launch per
+    dimension, replayed from a CUDA graph."""
+
+    def __init__(self, items):
+        self._keep = list(items)        # keep the handles and tensors alive
+        self._b = interp_batch_create([(it.handle, p, o) for it, p, o in items])
+
+    def autotune(self, stream=None) -> dict:
+        interp_batch_autotune(self._b, stream)
+        return self.tiles()
+
+    def tiles(self) -> dict:
+        names = sorted({it.info.name.decode() for it, _, _ in self._keep})
+        return {n: interp_batch_tile(self._b, n) for n in names}
+
+    def set_tiles(self, tiles: dict):
+        for n, t in tiles.items():
+            interp_batch_set_tile(self._b, n, t)
+
+    def run(self, stream=None):
+        interp_batch_run(self._b, stream)
+
+    def close(self):
+        if getattr(self, "_b", None):
+            interp_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ----------------------------------------------------------------------------- convenience object

@@ -20,7 +20,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 OUT = os.path.join(BUILD, "libinterp_b300.so")
 GEN_HDR = os.path.join(CSRC, "generated", "splines.h")
-COMMON_DEPS = [os.path.join(CSRC, f) for f in ("kernels.cuh", "registry.h", "layout.h", "ops_inst.cu", "interp.cu")] + \
+COMMON_DEPS = [os.path.join(CSRC, f) for f in ("kernels.cuh", "registry.h", "layout.h", "ops_inst.cu", "batch_inst.cu", "interp.cu")] + \
     [GEN_HDR, os.path.join(ROOT, "include", "interp.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -86,9 +86,14 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False, job
             jobsl.append(([nvcc(), *NVCC_FLAGS, *extra, *inc, f"-DINTERP_SPLINE={name}", f"-DINTERP_PART={part}",
                            "-c", os.path.join(CSRC, "ops_inst.cu"), "-o", o], None))
             objs.append(o)
+    for dim in (3, 4):
+        o = os.path.join(objdir, f"batch_{dim}d.o")
+        jobsl.append(([nvcc(), *NVCC_FLAGS, *extra, *inc, f"-DINTERP_BATCH_DIM={dim}", "-c",
+                       os.path.join(CSRC, "batch_inst.cu"), "-o", o], None))
+        objs.append(o)
     # the 4-D spline's units need several GB each: at most two of them run at a time
-    big = [j for j in jobsl if "d4s" in " ".join(j[0])]
-    small = [j for j in jobsl if "d4s" not in " ".join(j[0])]
+    big = [j for j in jobsl if "d4s" in " ".join(j[0]) or "BATCH_DIM=4" in " ".join(j[0])]
+    small = [j for j in jobsl if j not in big]
     logs = []
     with cf.ThreadPoolExecutor(max_workers=2) as exb, \
             cf.ThreadPoolExecutor(max_workers=max(1, (jobs or os.cpu_count() or 4) - 2)) as exs:

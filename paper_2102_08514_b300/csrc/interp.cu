@@ -9,7 +9,9 @@
 #include <array>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <string>
 #include <new>
 #include <vector>
 
@@ -244,6 +246,19 @@ struct interp {
     int device = 0;
 };
 
+static cudaError_t eval_launch(const interp *h, const float *pts, int64_t npts, float *out, float *grad, const float *gout,
+                        int mode, cudaStream_t st)
+{
+    const int dt = h->storage == INTERP_F32 ? 0 : (h->storage == INTERP_F16 ? 1 : 2);
+    // splines with many pieces (D4*: 6) run the piece-binned kernel; with few small pieces (FCC: 3)
+    // the sort costs more than the divergence it removes (measured).  INTERP_B300_BINNED=0 / 1
+    // forces the plain / binned kernel.
+    const char *bn = std::getenv("INTERP_B300_BINNED");
+    const bool want = bn ? bn[0] == '1' : h->ops->K >= 4;
+    const bool binned = want && h->ops->eval_binned[dt][mode];
+    return (binned ? h->ops->eval_binned : h->ops->eval)[dt][mode](pts, npts, h->coeffs, h->lay, out, grad, gout, st);
+}
+
 extern "C" {
 
 const char *interp_strerror(interp_status st)
@@ -309,14 +324,18 @@ interp_status interp_create(int s, const int32_t *L, const int32_t *xi, int n, c
         cc *= dims[a];
     }
     const int esz = storage == INTERP_F32 ? 4 : 2;
-    if (!ibl::make_layout(h->lay, s, h->dims, pad, esz, ops->M) ||
-        !ibl::make_layout(h->lay32, s, h->dims, pad, 4, ops->M)) {
+    // cosets side by side in the bricks or in separate arrays: separate by default (measured
+    // faster on the BCC quintic workload); INTERP_B300_INTERLEAVE=1 selects the other layout
+    const char *il = std::getenv("INTERP_B300_INTERLEAVE");
+    const bool inter = il && il[0] == '1';
+    if (!ibl::make_layout(h->lay, s, h->dims, pad, esz, ops->M, inter) ||
+        !ibl::make_layout(h->lay32, s, h->dims, pad, 4, ops->M, inter)) {
         delete h;
         return INTERP_ESIZE;
     }
     h->coeff_count = cc * ops->M;
     cudaGetDevice(&h->device);
-    const size_t bytes = (size_t)h->lay.coset_elems * ops->M * esz;
+    const size_t bytes = (size_t)h->lay.total * esz;
     cudaError_t e = cudaMalloc(&h->coeffs, bytes);
     if (e == cudaSuccess) e = cudaMemset(h->coeffs, 0, bytes);
     if (e != cudaSuccess) {
@@ -419,9 +438,7 @@ static interp_status eval_common(const interp_t *h, const float *pts, int64_t np
     if (mode >= 1 && !grad) return INTERP_EINVAL;
     if (mode == 2 && !gout) return INTERP_EINVAL;
     if (npts > (int64_t)INT32_MAX * kTPB) return INTERP_ESIZE;
-    const int dt = h->storage == INTERP_F32 ? 0 : (h->storage == INTERP_F16 ? 1 : 2);
-    cudaError_t e = h->ops->eval[dt][mode](pts, npts, h->coeffs, h->lay, out, grad, gout,
-                                           static_cast<cudaStream_t>(stream));
+    cudaError_t e = eval_launch(h, pts, npts, out, grad, gout, mode, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) cudaGetLastError();
     return cuda_status(e);
 }
@@ -450,7 +467,7 @@ interp_status interp_backward(interp_t *h, const float *pts, int64_t npts, const
     }
     if (!dcoeffs) return INTERP_OK;
     cudaError_t e = cudaSuccess;
-    const size_t dbytes = (size_t)h->lay32.coset_elems * h->ops->M * sizeof(float);
+    const size_t dbytes = (size_t)h->lay32.total * sizeof(float);
     if (!h->dpad) {
         e = cudaMalloc(&h->dpad, dbytes);
         if (e != cudaSuccess) {
@@ -470,11 +487,35 @@ interp_status interp_backward(interp_t *h, const float *pts, int64_t npts, const
     return cuda_status(e);
 }
 
+interp_status interp_eval_rays(const interp_t *h, const interp_rays_t *rays, int with_grad, float *out, float *pts_out,
+                               void *stream)
+{
+    if (!h || !rays || !out) return INTERP_EINVAL;
+    if (rays->width < 1 || rays->height < 1 || rays->steps < 1) return INTERP_EINVAL;
+    if ((int64_t)rays->width * rays->height > (int64_t)INT32_MAX) return INTERP_ESIZE;
+    if (h->s != 3 || h->storage != INTERP_F32 || !h->ops->rays[0]) return INTERP_EUNSUPPORTED;
+    ibl::RayGeom rg;
+    static_assert(sizeof(rg.origin) == sizeof(rays->origin), "ray geometry layout");
+    std::memcpy(rg.origin, rays->origin, sizeof(rg.origin));
+    std::memcpy(rg.du, rays->du, sizeof(rg.du));
+    std::memcpy(rg.dv, rays->dv, sizeof(rg.dv));
+    std::memcpy(rg.dir, rays->dir, sizeof(rg.dir));
+    std::memcpy(rg.lo, rays->box_lo, sizeof(rg.lo));
+    std::memcpy(rg.hi, rays->box_hi, sizeof(rg.hi));
+    rg.width = rays->width;
+    rg.height = rays->height;
+    rg.steps = rays->steps;
+    cudaError_t e = h->ops->rays[with_grad ? 1 : 0](rg, h->coeffs, h->lay, out, pts_out,
+                                                      static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) cudaGetLastError();
+    return cuda_status(e);
+}
+
 interp_status interp_backward_noalloc(interp_t *h, const float *pts, int64_t npts, const float *gout, float *dcoeffs,
                                       float *dpts, void *stream)
 {
     if (!h || npts < 0) return INTERP_EINVAL;
-    const int64_t need = (int64_t)h->lay32.coset_elems * h->ops->M;
+    const int64_t need = (int64_t)h->lay32.total;
     if (need > INTERP_NOALLOC_MAX_GRAD_ELEMS) return INTERP_ESIZE;
     if (npts == 0) return INTERP_OK;
     if (!pts || !gout) return INTERP_EINVAL;
@@ -516,4 +557,238 @@ interp_status interp_debug_indices(const interp_t *h, const float *pts, int64_t 
     return cuda_status(e);
 }
 
+
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------ batched evaluation
+
+struct interp_batch {
+    struct Group {
+        std::vector<ibl::BatchVol> vols;
+        ibl::BatchVol *d_vols = nullptr;
+        int64_t total = 0;
+        int grid = 0;
+    };
+    Group g[2];                                   // [0]: 3-D handles, [1]: 4-D handles
+    unsigned long long *d_counters = nullptr;     // one work counter per group
+    std::vector<std::string> names[2];            // spline name of every volume, per group
+    std::map<std::string, int> tiles;             // queries per tile, per spline
+    std::vector<const interp *> vols4;             // the 4-D handles (evaluated by their own launch)
+    cudaStream_t cs = nullptr;                    // private stream for graph capture
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool dirty = true;
+    int device = 0;
+};
+
+namespace {
+
+constexpr int kDefaultTile = 1024;
+
+// recompute the tile prefixes and upload the descriptor tables (synchronous)
+cudaError_t batch_upload(interp_batch *b)
+{
+    for (int gi = 0; gi < 2; ++gi) {
+        auto &G = b->g[gi];
+        int64_t first = 0;
+        for (size_t v = 0; v < G.vols.size(); ++v) {
+            G.vols[v].tile = gi == 0 ? b->tiles[b->names[gi][v]] : kDefaultTile;
+            G.vols[v].first_tile = first;
+            first += (G.vols[v].npts + G.vols[v].tile - 1) / G.vols[v].tile;
+        }
+        G.total = first;
+        if (!G.vols.empty()) {
+            cudaError_t e = cudaMemcpy(G.d_vols, G.vols.data(), G.vols.size() * sizeof(ibl::BatchVol),
+                                       cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    b->dirty = true;
+    return cudaSuccess;
+}
+
+// enqueue one batched evaluation: the 3-D handles in one persistent launch (counter reset +
+// kernel); the 4-D handles, whose 6-piece spline needs the piece-binned kernel, as one
+// evaluation launch each
+cudaError_t batch_enqueue(interp_batch *b, cudaStream_t st)
+{
+    auto &G = b->g[0];
+    if (G.total > 0) {
+        cudaError_t e = cudaMemsetAsync(b->d_counters, 0, sizeof(unsigned long long), st);
+        if (e == cudaSuccess)
+            e = ibr::batch_launch_3d(G.d_vols, (int)G.vols.size(), G.total, b->d_counters, G.grid, st);
+        if (e != cudaSuccess) return e;
+    }
+    for (size_t v = 0; v < b->vols4.size(); ++v) {
+        const ibl::BatchVol &bv = b->g[1].vols[v];
+        if (bv.npts == 0) continue;
+        cudaError_t e = eval_launch(b->vols4[v], bv.pts, bv.npts, bv.out, nullptr, nullptr, 0, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+void batch_free_graph(interp_batch *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+void interp_batch_destroy(interp_batch_t *b)
+{
+    if (!b) return;
+    cudaDeviceSynchronize();
+    batch_free_graph(b);
+    for (auto &G : b->g) cudaFree(G.d_vols);
+    cudaFree(b->d_counters);
+    if (b->cs) cudaStreamDestroy(b->cs);
+    delete b;
+}
+
+interp_status interp_batch_create(const interp_batch_item *items, int n, interp_batch_t **out)
+{
+    if (!out) return INTERP_EINVAL;
+    *out = nullptr;
+    if (!items || n < 1) return INTERP_EINVAL;
+    interp_batch *b = new (std::nothrow) interp_batch;
+    if (!b) return INTERP_ENOMEM;
+    cudaGetDevice(&b->device);
+    for (int i = 0; i < n; ++i) {
+        const interp_batch_item &it = items[i];
+        if (!it.vol || it.npts < 0 || (it.npts > 0 && (!it.pts || !it.out))) {
+            delete b;
+            return INTERP_EINVAL;
+        }
+        if (it.vol->storage != INTERP_F32) {
+            delete b;
+            return INTERP_EUNSUPPORTED;
+        }
+        const int gi = it.vol->s == 3 ? 0 : 1;
+        const int kind = gi == 0 ? ibr::batch_kind_3d(it.vol->ops->name) : ibr::batch_kind_4d(it.vol->ops->name);
+        if (kind < 0) {
+            delete b;
+            return INTERP_EUNSUPPORTED;
+        }
+        ibl::BatchVol bv{};
+        bv.c = static_cast<const float *>(it.vol->coeffs);
+        bv.pts = it.pts;
+        bv.out = it.out;
+        bv.npts = it.npts;
+        bv.kind = kind;
+        bv.tile = kDefaultTile;
+        bv.L = it.vol->lay;
+        b->g[gi].vols.push_back(bv);
+        b->names[gi].push_back(it.vol->ops->name);
+        if (gi == 0) b->tiles.emplace(it.vol->ops->name, kDefaultTile);
+        else b->vols4.push_back(it.vol);
+    }
+    cudaError_t e = cudaMalloc(&b->d_counters, 2 * sizeof(unsigned long long));
+    for (int gi = 0; gi < 2 && e == cudaSuccess; ++gi) {
+        auto &G = b->g[gi];
+        if (G.vols.empty()) continue;
+        e = cudaMalloc(&G.d_vols, G.vols.size() * sizeof(ibl::BatchVol));
+        if (e == cudaSuccess && gi == 0) e = ibr::batch_grid_3d(&G.grid);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = batch_upload(b);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        interp_batch_destroy(b);
+        return cuda_status(e);
+    }
+    *out = b;
+    return INTERP_OK;
+}
+
+interp_status interp_batch_tile(const interp_batch_t *b, const char *spline, int *tile)
+{
+    if (!b || !spline || !tile) return INTERP_EINVAL;
+    auto it = b->tiles.find(spline);
+    if (it == b->tiles.end()) return INTERP_EINVAL;
+    *tile = it->second;
+    return INTERP_OK;
+}
+
+interp_status interp_batch_set_tile(interp_batch_t *b, const char *spline, int tile)
+{
+    if (!b || !spline || tile < 128 || tile % 128 != 0) return INTERP_EINVAL;
+    auto it = b->tiles.find(spline);
+    if (it == b->tiles.end()) return INTERP_EINVAL;
+    it->second = tile;
+    const cudaError_t e = batch_upload(b);
+    if (e != cudaSuccess) cudaGetLastError();
+    return cuda_status(e);
+}
+
+interp_status interp_batch_autotune(interp_batch_t *b, void *stream)
+{
+    if (!b) return INTERP_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    static const int cand[] = {256, 512, 1024, 2048, 4096, 8192};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    std::vector<std::string> names;
+    for (auto &kv : b->tiles) names.push_back(kv.first);
+    for (const auto &name : names) {
+        int best = b->tiles[name];
+        float best_ms = 1e30f;
+        for (int t : cand) {
+            if (e != cudaSuccess) break;
+            b->tiles[name] = t;
+            e = batch_upload(b);
+            if (e == cudaSuccess) e = batch_enqueue(b, st);                  // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = batch_enqueue(b, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && ms < best_ms) {
+                best_ms = ms;
+                best = t;
+            }
+        }
+        b->tiles[name] = best;
+    }
+    if (e == cudaSuccess) e = batch_upload(b);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) cudaGetLastError();
+    return cuda_status(e);
+}
+
+interp_status interp_batch_run(interp_batch_t *b, void *stream)
+{
+    if (!b) return INTERP_EINVAL;
+    cudaError_t e = cudaSuccess;
+    if (b->dirty) {
+        batch_free_graph(b);
+        e = cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const cudaError_t e_enq = batch_enqueue(b, b->cs);
+            e = cudaStreamEndCapture(b->cs, &b->graph);
+            if (e_enq != cudaSuccess) e = e_enq;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+        if (e != cudaSuccess) {
+            batch_free_graph(b);
+            cudaGetLastError();
+            return cuda_status(e);
+        }
+        b->dirty = false;
+    }
+    e = cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) cudaGetLastError();
+    return cuda_status(e);
+}
+
+}  // extern "C"
+

@@ -258,13 +258,12 @@ __device__ __forceinline__ Fold<SP::S> fold_coset(const float (&x)[SP::S], const
 {
     constexpr int S = SP::S;
     constexpr int H = SP::HALO;
-    constexpr int ESZ = (int)sizeof(CT);
     Fold<S> f;
     bool ok = true;
-    int base = (K >= 0 ? K : kr) * v.L.coset_elems;
+    int base = (K >= 0 ? K : kr) * v.L.kw;
     sfor<S>([&](auto A) {
         constexpr int a = decltype(A)::value;
-        constexpr int lb = ibl::brick_lb(S, ESZ, a);
+        const int lb = v.L.lb[a];
         int idx;
         float y;
         if constexpr (K >= 0) {
@@ -507,6 +506,288 @@ __global__ void k_debug(const float *__restrict__ pts, int64_t n, DevVol<float> 
             piece[q * SP::M + K] = f.piece;
         }
     });
+}
+
+}  // namespace ib
+
+// ------------------------------------------------------------------------------------ batched launch
+
+namespace ib {
+
+using ibl::BatchVol;
+
+// evaluate queries [q0, q1) of one volume with spline SP, block-strided
+template <class SP>
+__device__ __forceinline__ void batch_tile(const BatchVol &bv, int64_t q0, int64_t q1)
+{
+    constexpr int S = SP::S;
+    DevVol<float> v;
+    v.c = bv.c;
+    v.L = bv.L;
+    for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+        float x[S];
+        bool finite = true;
+        sfor<S>([&](auto A) {
+            x[A] = bv.pts[q * S + A];
+            finite &= isfinite(x[A]);
+        });
+        float val = 0.0f, g[S];
+        if (finite) eval_point<SP, false, float>(x, v, val, g);
+        else val = __int_as_float(0x7fc00000);
+        bv.out[q] = val;
+    }
+}
+
+template <class... SPs> struct SplineList {};
+
+template <int I, class SP0, class... SPs>
+__device__ __forceinline__ void batch_dispatch(int kind, const BatchVol &bv, int64_t q0, int64_t q1)
+{
+    if (kind == I) batch_tile<SP0>(bv, q0, q1);
+    else if constexpr (sizeof...(SPs) > 0) batch_dispatch<I + 1, SPs...>(kind, bv, q0, q1);
+}
+
+// Persistent kernel: every CTA repeatedly claims the next work item (volume, tile) from a
+// global counter; the spline is uniform inside a CTA, so the dispatch does not diverge (pieces
+// of a multi-piece spline still diverge inside a warp; the 6-piece 4-D spline is therefore
+// evaluated by the piece-binned kernel, not here).  Work
+// item ids are ordered volume by volume; a CTA finds its volume by binary search over the
+// per-volume first-tile prefix.  The counter is zeroed before each launch (a memset node of the
+// same graph); the loop ends when the counter passes the total, so it always terminates.
+template <class... SPs>
+__global__ void __launch_bounds__(128) k_batch(const BatchVol *__restrict__ vols, int nvol, int64_t total_tiles,
+                                               unsigned long long *__restrict__ counter)
+{
+    __shared__ long long item;
+    for (;;) {
+        if (threadIdx.x == 0) item = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long it = item;
+        __syncthreads();
+        if (it >= total_tiles) return;
+        int lo = 0, hi = nvol - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (vols[mid].first_tile <= it) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchVol &bv = vols[lo];
+        const int64_t q0 = (it - bv.first_tile) * bv.tile;
+        const int64_t q1 = q0 + bv.tile < bv.npts ? q0 + bv.tile : bv.npts;
+        batch_dispatch<0, SPs...>(bv.kind, bv, q0, q1);
+    }
+}
+
+}  // namespace ib
+
+// ------------------------------------------------------------------------------------ rays
+
+namespace ib {
+
+// Orthographic rays: pixel (px, py) starts at o = origin + (px+1/2) du + (py+1/2) dv and runs
+// along dir; its chord with the box [lo, hi] is split into `steps` equal steps, sampled at the
+// step midpoints.  Per pixel: sum over samples of f (and of grad f).  A warp covers an 8 x 4
+// block of pixels, so its samples are close together and share coefficient sectors in L1.
+using ibl::RayGeom;
+
+template <class SP, bool GRAD>
+__global__ void __launch_bounds__(128) k_rays(RayGeom rg, DevVol<float> v, float *__restrict__ out,
+                                              float *__restrict__ pts_out)
+{
+    static_assert(SP::S == 3, "rays are 3-D");
+    // 128 threads = 4 warps; a block covers 16 x 8 pixels, a warp 8 x 4
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int px = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
+    const int py = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
+    if (px >= rg.width || py >= rg.height) return;
+    float o[3];
+    float tmin = -3.0e38f, tmax = 3.0e38f;
+    sfor<3>([&](auto A) {
+        o[A] = rg.origin[A] + ((float)px + 0.5f) * rg.du[A] + ((float)py + 0.5f) * rg.dv[A];
+        if (rg.dir[A] != 0.0f) {
+            const float inv = 1.0f / rg.dir[A];
+            const float t1 = (rg.lo[A] - o[A]) * inv, t2 = (rg.hi[A] - o[A]) * inv;
+            tmin = fmaxf(tmin, fminf(t1, t2));
+            tmax = fminf(tmax, fmaxf(t1, t2));
+        } else if (o[A] < rg.lo[A] || o[A] > rg.hi[A]) {
+            tmax = -3.0e38f;                                  // parallel to the slab and outside
+        }
+    });
+    float val = 0.0f, g[3] = {0.0f, 0.0f, 0.0f};
+    const int64_t pix = (int64_t)py * rg.width + px;
+    if (tmax > tmin) {
+        const float dt = (tmax - tmin) / (float)rg.steps;
+        for (int i = 0; i < rg.steps; ++i) {
+            const float t = tmin + ((float)i + 0.5f) * dt;
+            float x[3];
+            sfor<3>([&](auto A) { x[A] = fmaf(t, rg.dir[A], o[A]); });
+            if (pts_out) sfor<3>([&](auto A) { pts_out[(pix * rg.steps + i) * 3 + A] = x[A]; });
+            eval_point<SP, GRAD, float>(x, v, val, g);
+        }
+    } else if (pts_out) {
+        for (int i = 0; i < rg.steps; ++i)
+            sfor<3>([&](auto A) { pts_out[(pix * rg.steps + i) * 3 + A] = __int_as_float(0x7fc00000); });
+    }
+    out[pix * (GRAD ? 4 : 1)] = val;
+    if constexpr (GRAD) sfor<3>([&](auto A) { out[pix * 4 + 1 + A] = g[A]; });
+}
+
+}  // namespace ib
+
+// ------------------------------------------------------------------------------------ piece-binned evaluation
+
+namespace ib {
+
+// A multi-piece spline makes the piece data dependent: a warp whose 32 queries fall in K pieces
+// runs all K piece codes.  This kernel takes a tile of T queries x M cosets, classifies every
+// (query, coset) item (steps 1-3), sorts the items by piece in shared memory (counting sort),
+// then evaluates them in sorted order, so each warp sees one piece except where two pieces'
+// runs meet.  Per-(query, coset) results go to shared memory and are summed over the cosets in
+// a fixed order, so the output does not depend on the schedule.
+template <int S> struct BinRec {
+    int base;       // Fold::base
+    float t[S];     // folded offset
+    unsigned slots; // per slot (5 bits): sign (1), original axis (2), within-brick coordinate (2)
+};
+
+template <class SP, class CT>
+__device__ __forceinline__ Fold<SP::S> unpack_rec(const BinRec<SP::S> &r, const DevVol<CT> &v)
+{
+    constexpr int S = SP::S;
+    Fold<S> f;
+    f.base = r.base;
+    f.in_range = true;
+    sfor<S>([&](auto A) {
+        const unsigned b = (r.slots >> (5 * A)) & 31u;
+        Slot &sl = f.sl[A];
+        sl.y = r.t[A];
+        f.t[A] = r.t[A];
+        sl.sg = (b & 1u) ? -1 : 1;
+        sl.ax = (int)((b >> 1) & 3u);
+        sl.p = (int)(b >> 3);
+        // the brick geometry of the slot's axis, selected without dynamic indexing
+        sl.lb = v.L.lb[0];
+        sl.bs = v.L.bstride[0];
+        sl.wt = v.L.wt[0];
+        sfor<S - 1>([&](auto B) {
+            constexpr int ax = 1 + decltype(B)::value;
+            if (sl.ax == ax) {
+                sl.lb = v.L.lb[ax];
+                sl.bs = v.L.bstride[ax];
+                sl.wt = v.L.wt[ax];
+            }
+        });
+    });
+    return f;
+}
+
+template <class SP, class CT, int MODE, int T>
+__global__ void __launch_bounds__(128) k_eval_binned(const float *__restrict__ pts, int64_t n, DevVol<CT> v,
+                                                     float *__restrict__ out, float *__restrict__ grad,
+                                                     const float *__restrict__ gout)
+{
+    constexpr int S = SP::S, M = SP::M, K = SP::K, NI = T * M;
+    constexpr bool GRAD = MODE != 0;
+    constexpr int NV = GRAD ? S + 1 : 1;            // value (and gradient) per item
+    static_assert(NI <= 65535, "item index must fit 16 bits");
+    __shared__ BinRec<S> rec[NI];
+    __shared__ unsigned short perm[NI];
+    __shared__ unsigned short rank[NI];
+    __shared__ signed char rpiece[NI];
+    __shared__ float acc[NI * NV];
+    __shared__ int cnt[K], start[K + 1];
+    const int tid = threadIdx.x;
+    const int64_t q0 = (int64_t)blockIdx.x * T;
+    for (int i = tid; i < NI * NV; i += blockDim.x) acc[i] = 0.0f;
+    if (tid < K) cnt[tid] = 0;
+    __syncthreads();
+    // classify: item i = (query q0 + i % T, coset i / T)
+    for (int i = tid; i < NI; i += blockDim.x) {
+        const int ql = i % T, k = i / T;
+        const int64_t q = q0 + ql;
+        int j = -1;
+        if (q < n) {
+            float x[S];
+            bool finite = true;
+            sfor<S>([&](auto A) {
+                x[A] = pts[q * S + A];
+                finite &= isfinite(x[A]);
+            });
+            if (finite) {
+                const Fold<S> f = fold_coset<SP, -1, CT>(x, v, k);
+                if (f.in_range) {
+                    j = f.piece;
+                    BinRec<S> r;
+                    r.base = f.base;
+                    unsigned slots = 0;
+                    sfor<S>([&](auto A) {
+                        r.t[A] = f.t[A];
+                        slots |= ((f.sl[A].sg < 0 ? 1u : 0u) | ((unsigned)f.sl[A].ax << 1) | ((unsigned)f.sl[A].p << 3))
+                                 << (5 * A);
+                    });
+                    r.slots = slots;
+                    rec[i] = r;
+                    rank[i] = (unsigned short)atomicAdd(&cnt[j], 1);
+                }
+            }
+        }
+        rpiece[i] = (signed char)j;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int s = 0;
+        for (int j = 0; j < K; ++j) {
+            start[j] = s;
+            s += cnt[j];
+        }
+        start[K] = s;
+    }
+    __syncthreads();
+    for (int i = tid; i < NI; i += blockDim.x)
+        if (rpiece[i] >= 0) perm[start[rpiece[i]] + rank[i]] = (unsigned short)i;
+    __syncthreads();
+    // evaluate in piece order: consecutive lanes take consecutive sorted items
+    const int total = start[K];
+    for (int p = tid; p < total; p += blockDim.x) {
+        const int i = perm[p];
+        const int j = rpiece[i];
+        const Fold<S> f = unpack_rec<SP, CT>(rec[i], v);
+        float val = 0.0f, g[S];
+        sfor<S>([&](auto A) { g[A] = 0.0f; });
+        sfor<K>([&](auto Jc) {
+            if (j == decltype(Jc)::value) eval_piece<SP, decltype(Jc)::value, GRAD, CT>(f, v, val, g);
+        });
+        acc[i * NV] = val;
+        if constexpr (GRAD) sfor<S>([&](auto A) { acc[i * NV + 1 + A] = g[A]; });
+    }
+    __syncthreads();
+    // sum over cosets in coset order and write out
+    for (int ql = tid; ql < T; ql += blockDim.x) {
+        const int64_t q = q0 + ql;
+        if (q >= n) break;
+        bool finite = true;
+        sfor<S>([&](auto A) { finite &= isfinite(pts[q * S + A]); });
+        float val = 0.0f, g[S];
+        sfor<S>([&](auto A) { g[A] = 0.0f; });
+        sfor<M>([&](auto Kc) {
+            const int i = Kc * T + ql;
+            val += acc[i * NV];
+            if constexpr (GRAD) sfor<S>([&](auto A) { g[A] += acc[i * NV + 1 + A]; });
+        });
+        if (!finite) {
+            val = __int_as_float(0x7fc00000);
+            sfor<S>([&](auto A) { g[A] = val; });
+        }
+        if constexpr (MODE == 0) {
+            out[q] = val;
+        } else if constexpr (MODE == 1) {
+            if (out) out[q] = val;
+            sfor<S>([&](auto A) { grad[q * S + A] = g[A]; });
+        } else {
+            const float w = gout[q];
+            sfor<S>([&](auto A) { grad[q * S + A] = w * g[A]; });
+        }
+    }
 }
 
 }  // namespace ib

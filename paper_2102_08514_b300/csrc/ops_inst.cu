@@ -30,6 +30,21 @@ ib::DevVol<CT> make_vol(const void *c, const ibl::Layout &L)
 
 inline unsigned grid_for(int64_t n) { return (unsigned)((n + kTPB - 1) / kTPB); }
 
+[[maybe_unused]] constexpr int kBinTile = 256;
+
+template <class CT, int MODE>
+[[maybe_unused]] cudaError_t launch_eval_binned(const float *pts, int64_t n, const void *c, const ibl::Layout &L,
+                                                float *out, float *grad, const float *gout, cudaStream_t st)
+{
+    if constexpr (SP::K > 1) {
+        const unsigned grid = (unsigned)((n + kBinTile - 1) / kBinTile);
+        ib::k_eval_binned<SP, CT, MODE, kBinTile><<<grid, kTPB, 0, st>>>(pts, n, make_vol<CT>(c, L), out, grad, gout);
+        return cudaPeekAtLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
 template <class CT, int MODE>
 cudaError_t launch_eval(const float *pts, int64_t n, const void *c, const ibl::Layout &L, float *out, float *grad,
                         const float *gout, cudaStream_t st)
@@ -50,6 +65,19 @@ cudaError_t launch_eval(const float *pts, int64_t n, const void *c, const ibl::L
 {
     ib::k_debug<SP><<<grid_for(n), kTPB, 0, st>>>(pts, n, make_vol<float>(nullptr, L), cells, piece);
     return cudaPeekAtLastError();
+}
+
+template <bool GRAD>
+[[maybe_unused]] cudaError_t launch_rays(const ibl::RayGeom &rg, const void *c, const ibl::Layout &L, float *out,
+                                         float *pts_out, cudaStream_t st)
+{
+    if constexpr (SP::S == 3) {
+        const dim3 grid((rg.width + 15) / 16, (rg.height + 7) / 8);
+        ib::k_rays<SP, GRAD><<<grid, 128, 0, st>>>(rg, make_vol<float>(c, L), out, pts_out);
+        return cudaPeekAtLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
@@ -76,12 +104,23 @@ void IB_CAT(fill_, INTERP_SPLINE, _, INTERP_PART)(SplineOps &o)
     o.lookups = SP::LOOKUPS;
     o.adjoint = launch_adjoint;
     o.debug = launch_debug;
+    if constexpr (SP::S == 3) {
+        o.rays[0] = launch_rays<false>;
+        o.rays[1] = launch_rays<true>;
+    }
 #else
     constexpr int mode = INTERP_PART;
     o.eval[0][mode] = launch_eval<float, mode>;
     if constexpr (SP::HALF_STORAGE) {
         o.eval[1][mode] = launch_eval<__half, mode>;
         o.eval[2][mode] = launch_eval<__nv_bfloat16, mode>;
+    }
+    if constexpr (SP::K > 1) {
+        o.eval_binned[0][mode] = launch_eval_binned<float, mode>;
+        if constexpr (SP::HALF_STORAGE) {
+            o.eval_binned[1][mode] = launch_eval_binned<__half, mode>;
+            o.eval_binned[2][mode] = launch_eval_binned<__nv_bfloat16, mode>;
+        }
     }
 #endif
 }

@@ -12,6 +12,7 @@ namespace ibr {
 using EvalFn = cudaError_t (*)(const float *, int64_t, const void *, const ibl::Layout &, float *, float *,
                                const float *, cudaStream_t);
 using AdjFn = cudaError_t (*)(const float *, int64_t, const float *, const ibl::Layout &, float *, cudaStream_t);
+using RayFn = cudaError_t (*)(const ibl::RayGeom &, const void *, const ibl::Layout &, float *, float *, cudaStream_t);
 using DbgFn = cudaError_t (*)(const float *, int64_t, const ibl::Layout &, int32_t *, int32_t *, cudaStream_t);
 
 struct SplineOps {
@@ -21,7 +22,9 @@ struct SplineOps {
     const int *cosets = nullptr; // M x s
     double fma_value = 0, fma_grad = 0, lookups = 0;
     EvalFn eval[3][3] = {};      // [storage: f32, f16, bf16][mode: value, value+grad, pullback]
+    EvalFn eval_binned[3][3] = {};  // the same, piece-binned (multi-piece splines only)
     AdjFn adjoint = nullptr;
+    RayFn rays[2] = {};          // [value, value+grad], 3-D splines, FP32 storage
     DbgFn debug = nullptr;
 };
 
@@ -37,3 +40,11 @@ enum Part { PART_VALUE = 0, PART_GRAD = 1, PART_PULL = 2, PART_MISC = 3 };
     void fill_##name##_2(SplineOps &);             \
     void fill_##name##_3(SplineOps &);             \
     }
+
+namespace ibr {
+int batch_kind_3d(const char *name);
+int batch_kind_4d(const char *name);
+cudaError_t batch_grid_3d(int *grid);
+cudaError_t batch_launch_3d(const ibl::BatchVol *vols, int nvol, int64_t total_tiles, unsigned long long *counter,
+                            int grid, cudaStream_t st);
+}  // namespace ibr

@@ -180,6 +180,11 @@ def main(argv=None):
         "",
         "// X-macro over every built-in spline: X(struct name)",
         "#define INTERP_GEN_SPLINES(X) " + " ".join(f"X({n})" for n in args.names),
+        "// the same, split by dimension (the batched kernels are per dimension); comma-separated",
+        "#define INTERP_GEN_SPLINES_3D " + ", ".join(f"interp_gen::{n}" for n in args.names if metas[n]["s"] == 3),
+        "#define INTERP_GEN_SPLINES_4D " + ", ".join(f"interp_gen::{n}" for n in args.names if metas[n]["s"] == 4),
+        "#define INTERP_GEN_NAMES_3D " + ", ".join(f'"{n}"' for n in args.names if metas[n]["s"] == 3),
+        "#define INTERP_GEN_NAMES_4D " + ", ".join(f'"{n}"' for n in args.names if metas[n]["s"] == 4),
         f'#define INTERP_GEN_DIGEST "{digest}"',
         "",
     ]
