@@ -283,7 +283,8 @@ class Batch:
         return self.tiles()
 
     def tiles(self) -> dict:
-        names = sorted({it.info.name.decode() for it, _, _ in self._keep})
+        """Tile size per 3-D spline (4-D handles run their own launch and have none)."""
+        names = sorted({it.info.name.decode() for it, _, _ in self._keep if it.s == 3})
         return {n: interp_batch_tile(self._b, n) for n in names}
 
     def set_tiles(self, tiles: dict):
