@@ -258,6 +258,8 @@ def time_fit_step(torch, itp, wl, pts, pts_h, steps, warmup, stream, barrier):
         opt.step()
 
     _, per = time_steps(torch, step, steps, warmup, stream, barrier)
+    # the fit wrote its own coefficients into the handle: restore the workload's
+    itp.set_coeffs(torch.from_numpy(coefficients(wl)).cuda())
     return statistics.mean(per)
 
 
@@ -346,18 +348,14 @@ def run_ours(args):
             itp.backward(pts_d, g_d, dcoef)
             dc_pin.copy_(dcoef, non_blocking=True)
     else:
+        # the library's host-buffer entry point: chunked copies overlapping the evaluation
+        from paper_2102_08514_b300.binding import interp_eval_host
         out_pin = torch.empty(n, pin_memory=True)
         grad_pin = torch.empty(n, s, pin_memory=True)
         h2d, d2h = n * s * 4, n * 4 * (1 + (s if form == "value_grad" else 0))
 
         def e2e_step():
-            pts_d.copy_(pts_pin, non_blocking=True)
-            if form == "value_grad":
-                itp.eval_grad(pts_d, out, grad)
-                grad_pin.copy_(grad, non_blocking=True)
-            else:
-                itp.eval(pts_d, out)
-            out_pin.copy_(out, non_blocking=True)
+            interp_eval_host(itp.handle, pts_pin, out_pin, grad_pin if form == "value_grad" else None)
 
     e2e_steps = max(3, min(args.steps, 10))
     e2e_ms, _ = time_steps(torch, e2e_step, e2e_steps, fw, stream, barrier)
@@ -406,7 +404,21 @@ def run_ours(args):
     if args.workload != WORKLOAD or args.storage != "f32" or form != DEFAULT_FORM[WORKLOAD]:
         line["metric"] = f"evals/s ({form}, {args.storage} storage)"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, pts_h, c, form, seconds=args.cpu_seconds)
+        line["cpu_baseline"], (m, ref_v, ref_g) = cpu_baseline(wl, pts_h, c, form, seconds=args.cpu_seconds)
+        if form != "adjoint":
+            run_form[form]()
+            torch.cuda.synchronize()
+            got_v = out[:m].double().cpu().numpy()
+            err = got_v - ref_v
+            cmax = float(np.abs(c).max())
+            acc = {"sample": m, "max_abs_value": float(np.abs(err).max()), "rms_value": float(np.sqrt((err ** 2).mean())),
+                   "max_abs_over_max_c": float(np.abs(err).max()) / cmax, "tolerance_over_max_c": 2e-6,
+                   "against": "FP64 oracle on the original coefficients"}
+            if ref_g is not None and form == "value_grad":
+                eg = grad[:m].double().cpu().numpy() - ref_g
+                acc["max_abs_grad"] = float(np.abs(eg).max())
+                acc["rms_grad"] = float(np.sqrt((eg ** 2).mean()))
+            line["accuracy"] = acc
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -429,20 +441,21 @@ def cpu_baseline(wl, pts, c, form="value_grad", seconds=15.0):
     orc, spl, lat = _oracle_setup(wl)
     cores = os.cpu_count() or 1
     cd = c.astype(np.float64)
-    # grow the sample until it takes about `seconds` (bounded), then report the last one
-    m, off = 4 * cores, 0
+    # grow the sample until it takes about `seconds` (bounded), then report the last one; the
+    # oracle's outputs on the first queries also serve the accuracy report
+    m = 4 * cores
     while True:
-        sample = pts[off:off + m].astype(np.float64)
+        sample = pts[:m].astype(np.float64)
         t = time.perf_counter()
-        orc.eval_sum(spl, lat.D, lat.cosets, cd, sample, grad=(form != "value"), nthreads=cores)
+        res = orc.eval_sum(spl, lat.D, lat.cosets, cd, sample, grad=(form != "value"), nthreads=cores)
         dt = time.perf_counter() - t
-        off += m
-        if dt >= 0.5 * seconds or off + 2 * m > len(pts):
+        if dt >= 0.5 * seconds or 2 * m > len(pts):
             break
-        m = int(min(len(pts) - off, m * max(2.0, min(8.0, seconds / max(dt, 1e-3)))))
+        m = int(min(len(pts), m * max(2.0, min(8.0, seconds / max(dt, 1e-3)))))
+    ref_v, ref_g = (res if form != "value" else (res, None))
     return {"value": m / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{m} of the {wl.queries} queries ({'value' if form == 'value' else 'value+grad'}, FP64, "
-                      f"brute-force recurrence), {dt:.1f} s"}
+                      f"brute-force recurrence), {dt:.1f} s"}, (m, ref_v, ref_g)
 
 
 def run_reference(args):

@@ -75,6 +75,8 @@ def load(path: str = LIB_PATH):
     lib.interp_backward.argtypes = [P, P, I64, P, P, P, P]
     lib.interp_debug_indices.argtypes = [P, P, I64, P, P, P]
     lib.interp_backward_noalloc.argtypes = [P, P, I64, P, P, P, P]
+    lib.interp_eval_host.argtypes = [P, P, I64, P, P, P]
+    lib.interp_eval_host.restype = I
     lib.interp_eval_rays.argtypes = [P, ctypes.POINTER(Rays), I, P, P, P]
     lib.interp_eval_rays.restype = I
     lib.interp_batch_create.argtypes = [ctypes.POINTER(BatchItem), I, ctypes.POINTER(ctypes.c_void_p)]
@@ -99,7 +101,7 @@ def exported_symbols() -> list[str]:
             "interp_create", "interp_destroy", "interp_info", "interp_set_coeffs", "interp_eval",
             "interp_eval_grad", "interp_backward", "interp_debug_indices", "interp_backward_noalloc",
             "interp_batch_create", "interp_batch_autotune", "interp_batch_tile", "interp_batch_set_tile",
-            "interp_batch_run", "interp_batch_destroy", "interp_eval_rays"]
+            "interp_batch_run", "interp_batch_destroy", "interp_eval_rays", "interp_eval_host"]
 
 
 def _strerror(st: int) -> str:
@@ -190,6 +192,18 @@ def interp_eval_grad(h, pts, out, grad, stream=None):
     _check(load().interp_eval_grad(h, _dptr(pts, "pts", torch.float32), pts.shape[0],
                                    _dptr(out, "out", torch.float32), _dptr(grad, "grad", torch.float32),
                                    _stream(stream)), "interp_eval_grad")
+
+
+def interp_eval_host(h, pts, out, grad=None, stream=None):
+    """Host (ideally pinned) CPU tensors in and out; copies overlap the evaluation (see the C
+    header).  Synchronise the stream before reading out / grad."""
+    import torch
+    for t, nm in ((pts, "pts"), (out, "out"), (grad, "grad")):
+        if t is not None and (t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous()):
+            raise ValueError(f"{nm} must be a contiguous float32 CPU tensor")
+    _check(load().interp_eval_host(h, ctypes.c_void_p(pts.data_ptr()), pts.shape[0], ctypes.c_void_p(out.data_ptr()),
+                                   ctypes.c_void_p(grad.data_ptr()) if grad is not None else None, _stream(stream)),
+           "interp_eval_host")
 
 
 def interp_backward(h, pts, gout, dcoeffs, dpts=None, stream=None):

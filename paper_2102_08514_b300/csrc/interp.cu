@@ -244,6 +244,10 @@ struct interp {
     void *coeffs = nullptr;    // padded, bricked storage
     float *dpad = nullptr;     // padded FP32 gradient buffer (allocated by the first interp_backward)
     int device = 0;
+    // interp_eval_host staging: two slots of (points, values, gradients) and one stream each
+    float *stage[2] = {nullptr, nullptr};
+    cudaStream_t hs[2] = {nullptr, nullptr};
+    cudaEvent_t hev[3] = {nullptr, nullptr, nullptr};
 };
 
 static cudaError_t eval_launch(const interp *h, const float *pts, int64_t npts, float *out, float *grad, const float *gout,
@@ -354,6 +358,12 @@ void interp_destroy(interp_t *h)
     cudaDeviceSynchronize();
     cudaFree(h->coeffs);
     cudaFree(h->dpad);
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(h->stage[i]);
+        if (h->hs[i]) cudaStreamDestroy(h->hs[i]);
+    }
+    for (auto &ev : h->hev)
+        if (ev) cudaEventDestroy(ev);
     delete h;
 }
 
@@ -451,6 +461,51 @@ interp_status interp_eval(const interp_t *h, const float *pts, int64_t npts, flo
 interp_status interp_eval_grad(const interp_t *h, const float *pts, int64_t npts, float *out, float *grad, void *stream)
 {
     return eval_common(h, pts, npts, out, grad, nullptr, 1, stream);
+}
+
+interp_status interp_eval_host(interp_t *h, const float *pts, int64_t npts, float *out, float *grad, void *stream)
+{
+    if (!h || npts < 0) return INTERP_EINVAL;
+    if (npts == 0) return INTERP_OK;
+    if (!pts || !out) return INTERP_EINVAL;
+    constexpr int64_t kChunk = 1 << 20;
+    const int s = h->s;
+    const int64_t slot_floats = kChunk * (s + 1 + s);     // points, values, gradients
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        if (!h->stage[i]) e = cudaMalloc(&h->stage[i], (size_t)slot_floats * sizeof(float));
+        if (e == cudaSuccess && !h->hs[i]) e = cudaStreamCreateWithFlags(&h->hs[i], cudaStreamNonBlocking);
+    }
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+        if (!h->hev[i]) e = cudaEventCreateWithFlags(&h->hev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_status(e);
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the internal streams start after the work already on `stream`
+    e = cudaEventRecord(h->hev[2], st);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(h->hs[i], h->hev[2], 0);
+    int64_t chunk = 0;
+    for (int64_t q0 = 0; q0 < npts && e == cudaSuccess; q0 += kChunk, ++chunk) {
+        const int slot = (int)(chunk & 1);
+        cudaStream_t ss = h->hs[slot];
+        const int64_t m = std::min<int64_t>(kChunk, npts - q0);
+        float *dp = h->stage[slot], *dv = dp + kChunk * s, *dg = dv + kChunk;
+        // stream order inside a slot keeps its buffers from being overwritten while in use
+        e = cudaMemcpyAsync(dp, pts + q0 * s, (size_t)m * s * sizeof(float), cudaMemcpyHostToDevice, ss);
+        if (e == cudaSuccess) e = eval_launch(h, dp, m, dv, grad ? dg : nullptr, nullptr, grad ? 1 : 0, ss);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out + q0, dv, (size_t)m * sizeof(float), cudaMemcpyDeviceToHost, ss);
+        if (e == cudaSuccess && grad)
+            e = cudaMemcpyAsync(grad + q0 * s, dg, (size_t)m * s * sizeof(float), cudaMemcpyDeviceToHost, ss);
+    }
+    // `stream` continues after both internal streams
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaEventRecord(h->hev[i], h->hs[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->hev[i], 0);
+    }
+    if (e != cudaSuccess) cudaGetLastError();
+    return cuda_status(e);
 }
 
 interp_status interp_backward(interp_t *h, const float *pts, int64_t npts, const float *gout, float *dcoeffs,

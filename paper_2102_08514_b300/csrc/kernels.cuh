@@ -681,20 +681,33 @@ __device__ __forceinline__ Fold<SP::S> unpack_rec(const BinRec<SP::S> &r, const 
     return f;
 }
 
-template <class SP, class CT, int MODE, int T>
-__global__ void __launch_bounds__(128) k_eval_binned(const float *__restrict__ pts, int64_t n, DevVol<CT> v,
-                                                     float *__restrict__ out, float *__restrict__ grad,
-                                                     const float *__restrict__ gout)
+// shared memory of k_eval_binned for a tile of T queries
+template <class SP, int MODE, int T>
+constexpr size_t binned_smem_bytes()
+{
+    constexpr int NI = T * SP::M;
+    constexpr int NV = MODE != 0 ? SP::S + 1 : 1;
+    return (size_t)NI * (sizeof(BinRec<SP::S>) + NV * sizeof(float) + 2 * sizeof(unsigned short) + 1) + 64;
+}
+
+// T queries per tile, NT threads per CTA.  With NT = 512 and a large tile the CTA fills an SM,
+// and its warps walk through the sorted pieces together, so only one or two pieces' code is hot
+// in the instruction caches at a time.
+template <class SP, class CT, int MODE, int T, int NT>
+__global__ void __launch_bounds__(NT) k_eval_binned(const float *__restrict__ pts, int64_t n, DevVol<CT> v,
+                                                    float *__restrict__ out, float *__restrict__ grad,
+                                                    const float *__restrict__ gout)
 {
     constexpr int S = SP::S, M = SP::M, K = SP::K, NI = T * M;
     constexpr bool GRAD = MODE != 0;
     constexpr int NV = GRAD ? S + 1 : 1;            // value (and gradient) per item
     static_assert(NI <= 65535, "item index must fit 16 bits");
-    __shared__ BinRec<S> rec[NI];
-    __shared__ unsigned short perm[NI];
-    __shared__ unsigned short rank[NI];
-    __shared__ signed char rpiece[NI];
-    __shared__ float acc[NI * NV];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    BinRec<S> *rec = reinterpret_cast<BinRec<S> *>(smem_raw);
+    float *acc = reinterpret_cast<float *>(rec + NI);
+    unsigned short *perm = reinterpret_cast<unsigned short *>(acc + NI * NV);
+    unsigned short *rank = perm + NI;
+    signed char *rpiece = reinterpret_cast<signed char *>(rank + NI);
     __shared__ int cnt[K], start[K + 1];
     const int tid = threadIdx.x;
     const int64_t q0 = (int64_t)blockIdx.x * T;

@@ -1,6 +1,8 @@
 // ops_inst.cu -- instantiates the kernels of ONE spline and ONE kernel family.  The build
 // compiles this file once per (spline, family) with -DINTERP_SPLINE=<name> -DINTERP_PART=<0..3>
 // so the large unrolled kernels compile in parallel.
+#include <cstdlib>
+
 #include "kernels.cuh"
 #include "registry.h"
 
@@ -30,16 +32,36 @@ ib::DevVol<CT> make_vol(const void *c, const ibl::Layout &L)
 
 inline unsigned grid_for(int64_t n) { return (unsigned)((n + kTPB - 1) / kTPB); }
 
-[[maybe_unused]] constexpr int kBinTile = 256;
+// piece-binned kernel configurations: (tile of queries, threads per CTA)
+template <class CT, int MODE, int T, int NT>
+[[maybe_unused]] cudaError_t launch_binned_cfg(const float *pts, int64_t n, const void *c, const ibl::Layout &L,
+                                               float *out, float *grad, const float *gout, cudaStream_t st)
+{
+    constexpr size_t smem = ib::binned_smem_bytes<SP, MODE, T>();
+    auto kern = ib::k_eval_binned<SP, CT, MODE, T, NT>;
+    static unsigned long long configured = 0;          // per device: the attribute is set once
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 64 || !(configured >> dev & 1ull)) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev < 64) configured |= 1ull << dev;
+    }
+    const unsigned grid = (unsigned)((n + T - 1) / T);
+    kern<<<grid, NT, smem, st>>>(pts, n, make_vol<CT>(c, L), out, grad, gout);
+    return cudaPeekAtLastError();
+}
 
 template <class CT, int MODE>
 [[maybe_unused]] cudaError_t launch_eval_binned(const float *pts, int64_t n, const void *c, const ibl::Layout &L,
                                                 float *out, float *grad, const float *gout, cudaStream_t st)
 {
     if constexpr (SP::K > 1) {
-        const unsigned grid = (unsigned)((n + kBinTile - 1) / kBinTile);
-        ib::k_eval_binned<SP, CT, MODE, kBinTile><<<grid, kTPB, 0, st>>>(pts, n, make_vol<CT>(c, L), out, grad, gout);
-        return cudaPeekAtLastError();
+        // INTERP_B300_BINCFG=small selects 256-query tiles on 128-thread CTAs (several CTAs per SM)
+        const char *cfg = std::getenv("INTERP_B300_BINCFG");
+        if (cfg && cfg[0] == 's') return launch_binned_cfg<CT, MODE, 256, 128>(pts, n, c, L, out, grad, gout, st);
+        return launch_binned_cfg<CT, MODE, 1024, 512>(pts, n, c, L, out, grad, gout, st);
     } else {
         return cudaErrorInvalidValue;
     }

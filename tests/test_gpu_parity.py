@@ -252,3 +252,26 @@ def test_piece_binned_kernel_equals_plain_kernel(name, monkeypatch):
         res.append((v, v2, gr, dp))
     for a, b in zip(*res):
         assert torch.equal(torch.nan_to_num(a, nan=7.0), torch.nan_to_num(b, nan=7.0))
+
+
+def test_eval_host_matches_device_path():
+    # host buffers in, host buffers out, several chunks plus a ragged tail
+    torch = require_cuda()
+    from paper_2102_08514_b300.binding import interp_eval_host
+    name = "bcc_quintic"
+    dims = (20, 20, 20)
+    _, itp = _interp(name, dims)
+    itp.set_coeffs(torch.from_numpy(_coeffs(name, dims, 21)).cuda())
+    lo, hi = interior_box(name, dims)
+    n = (1 << 21) + 4321
+    pts = torch.from_numpy(uniform_points(make_rng(22, 0), n, lo, hi)).pin_memory()
+    out = torch.empty(n, pin_memory=True)
+    grad = torch.empty(n, 3, pin_memory=True)
+    interp_eval_host(itp.handle, pts, out, grad)
+    torch.cuda.synchronize()
+    v, g = itp.eval_grad(pts.cuda())
+    assert torch.equal(out, v.cpu()) and torch.equal(grad, g.cpu())
+    out2 = torch.empty(n, pin_memory=True)
+    interp_eval_host(itp.handle, pts, out2)                          # value only
+    torch.cuda.synchronize()
+    assert torch.equal(out2, itp.eval(pts.cuda()).cpu())
