@@ -251,6 +251,8 @@ def time_fit_step(torch, itp, wl, pts, pts_h, steps, warmup, stream, barrier):
     y = torch.from_numpy(marschner_lobb(phys).astype(np.float32)).cuda()
     c = torch.zeros(itp.shape, device="cuda", requires_grad=True)
     opt = torch.optim.Adam([c], lr=0.05)
+    perm, pts = itp.sort_points(pts)                     # once, as the fit driver does
+    y = y[perm.long()]
 
     def step():
         opt.zero_grad(set_to_none=False)
@@ -325,6 +327,18 @@ def run_ours(args):
     for name_f, fn in run_form.items():
         _, per_f = time_steps(torch, fn, fsteps, fw, stream, barrier)
         form_ms[name_f] = statistics.mean(per_f)
+
+    # the same queries sorted in space (interp_sort_points): sort time, value, adjoint
+    from paper_2102_08514_b300.binding import interp_sort_points
+    perm = torch.empty(n, device="cuda", dtype=torch.int32)
+    pts_s = torch.empty_like(pts)
+    _, per_s = time_steps(torch, lambda: interp_sort_points(itp.handle, pts, perm, pts_s), fsteps, fw, stream, barrier)
+    form_ms["sort"] = statistics.mean(per_s)
+    gout_s = gout[perm.long()]
+    _, per_f = time_steps(torch, lambda: itp.eval(pts_s, out), fsteps, fw, stream, barrier)
+    form_ms["value_sorted"] = statistics.mean(per_f)
+    _, per_f = time_steps(torch, lambda: itp.backward(pts_s, gout_s, dcoef), fsteps, fw, stream, barrier)
+    form_ms["adjoint_sorted"] = statistics.mean(per_f)
 
     # workload-specific forms: ray-coherent queries (bcc_quintic_128), one fitting step (fcc_6dir_128)
     if wl.name == "bcc_quintic_128" and args.storage == "f32":

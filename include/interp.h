@@ -140,7 +140,9 @@ interp_status interp_eval_host(interp_t *h, const float *pts, int64_t npts, floa
  * dcoeffs has the coefficient layout of interp_set_coeffs (FP32) and is ACCUMULATED into: zero it
  * first for a plain gradient.  The scatter uses FP32 atomics into a handle-owned padded buffer,
  * so the order of additions, and the last bits of dcoeffs, vary between runs.  dcoeffs may be
- * NULL to compute dpts only.
+ * NULL to compute dpts only.  Each block of 1024 consecutive queries whose cells fit a small box
+ * (e.g. after interp_sort_points) is summed in shared memory first, with one global atomic per
+ * touched coefficient; other blocks add every contribution with its own atomic.
  */
 interp_status interp_backward(interp_t *h, const float *pts, int64_t npts, const float *gout, float *dcoeffs,
                               float *dpts, void *stream);
@@ -220,6 +222,19 @@ typedef struct {
 } interp_rays_t;
 interp_status interp_eval_rays(const interp_t *h, const interp_rays_t *rays, int with_grad, float *out,
                                float *pts_out, void *stream);
+
+/*
+ * interp_sort_points -- reorder queries so that queries close in space are close in the array (not
+ * in the paper).  Bins of 4 x 4 x 4 cells (2 per axis in 4-D) in Morton order; a counting sort.
+ * perm[r] (int32, npts) = the original index of the query at sorted position r, and/or
+ * pts_sorted[r*s + a] = pts[perm[r]*s + a]; either may be NULL (not both).  The order inside a
+ * bin is unspecified.  Evaluating sorted queries reuses coefficients in L1, and interp_backward
+ * on sorted queries sums most contributions in shared memory instead of global atomics.  The
+ * handle owns the bin counters (allocated on first use); calls on one handle must not overlap.
+ * Errors: EINVAL, ESIZE (npts >= 2^31), ENOMEM, ECUDA.
+ */
+interp_status interp_sort_points(interp_t *h, const float *pts, int64_t npts, int32_t *perm, float *pts_sorted,
+                                 void *stream);
 
 /*
  * interp_debug_indices -- for every query q and coset k: cells[(q*M + k)*s + a] = the index i of

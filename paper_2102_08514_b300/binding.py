@@ -75,6 +75,8 @@ def load(path: str = LIB_PATH):
     lib.interp_backward.argtypes = [P, P, I64, P, P, P, P]
     lib.interp_debug_indices.argtypes = [P, P, I64, P, P, P]
     lib.interp_backward_noalloc.argtypes = [P, P, I64, P, P, P, P]
+    lib.interp_sort_points.argtypes = [P, P, I64, P, P, P]
+    lib.interp_sort_points.restype = I
     lib.interp_eval_host.argtypes = [P, P, I64, P, P, P]
     lib.interp_eval_host.restype = I
     lib.interp_eval_rays.argtypes = [P, ctypes.POINTER(Rays), I, P, P, P]
@@ -101,7 +103,8 @@ def exported_symbols() -> list[str]:
             "interp_create", "interp_destroy", "interp_info", "interp_set_coeffs", "interp_eval",
             "interp_eval_grad", "interp_backward", "interp_debug_indices", "interp_backward_noalloc",
             "interp_batch_create", "interp_batch_autotune", "interp_batch_tile", "interp_batch_set_tile",
-            "interp_batch_run", "interp_batch_destroy", "interp_eval_rays", "interp_eval_host"]
+            "interp_batch_run", "interp_batch_destroy", "interp_eval_rays", "interp_eval_host",
+            "interp_sort_points"]
 
 
 def _strerror(st: int) -> str:
@@ -204,6 +207,15 @@ def interp_eval_host(h, pts, out, grad=None, stream=None):
     _check(load().interp_eval_host(h, ctypes.c_void_p(pts.data_ptr()), pts.shape[0], ctypes.c_void_p(out.data_ptr()),
                                    ctypes.c_void_p(grad.data_ptr()) if grad is not None else None, _stream(stream)),
            "interp_eval_host")
+
+
+def interp_sort_points(h, pts, perm=None, pts_sorted=None, stream=None):
+    """Spatial counting sort of the queries (see the C header); fills perm (int32) and/or
+    pts_sorted."""
+    import torch
+    _check(load().interp_sort_points(h, _dptr(pts, "pts", torch.float32), pts.shape[0],
+                                     _dptr(perm, "perm", torch.int32), _dptr(pts_sorted, "pts_sorted", torch.float32),
+                                     _stream(stream)), "interp_sort_points")
 
 
 def interp_backward(h, pts, gout, dcoeffs, dpts=None, stream=None):
@@ -384,6 +396,15 @@ class Interpolator:
         dpts = torch.empty(pts.shape[0], self.s, device=pts.device, dtype=torch.float32) if want_dpts else None
         interp_backward(self._h, pts, gout, dcoeffs, dpts, stream)
         return dcoeffs, dpts
+
+    def sort_points(self, pts, stream=None):
+        """(permutation, sorted points): queries reordered so that neighbours in space are
+        neighbours in memory."""
+        import torch
+        perm = torch.empty(pts.shape[0], device=pts.device, dtype=torch.int32)
+        out = torch.empty_like(pts)
+        interp_sort_points(self._h, pts, perm, out, stream)
+        return perm, out
 
     def debug_indices(self, pts, stream=None):
         import torch

@@ -244,6 +244,8 @@ struct interp {
     void *coeffs = nullptr;    // padded, bricked storage
     float *dpad = nullptr;     // padded FP32 gradient buffer (allocated by the first interp_backward)
     int device = 0;
+    unsigned *sort_keys = nullptr;  // interp_sort_points bin counters
+    int sort_nkeys = 0;
     // interp_eval_host staging: two slots of (points, values, gradients) and one stream each
     float *stage[2] = {nullptr, nullptr};
     cudaStream_t hs[2] = {nullptr, nullptr};
@@ -358,6 +360,7 @@ void interp_destroy(interp_t *h)
     cudaDeviceSynchronize();
     cudaFree(h->coeffs);
     cudaFree(h->dpad);
+    cudaFree(h->sort_keys);
     for (int i = 0; i < 2; ++i) {
         cudaFree(h->stage[i]);
         if (h->hs[i]) cudaStreamDestroy(h->hs[i]);
@@ -597,6 +600,44 @@ interp_status interp_backward_noalloc(interp_t *h, const float *pts, int64_t npt
         k_unpad_add<<<grid, 256, 0, st>>>(scratch, dcoeffs, h->coeff_count, h->lay32);
         e = cudaPeekAtLastError();
     }
+    if (e != cudaSuccess) cudaGetLastError();
+    return cuda_status(e);
+}
+
+interp_status interp_sort_points(interp_t *h, const float *pts, int64_t npts, int32_t *perm, float *pts_sorted,
+                                 void *stream)
+{
+    if (!h || npts < 0 || (!perm && !pts_sorted)) return INTERP_EINVAL;
+    if (npts == 0) return INTERP_OK;
+    if (!pts) return INTERP_EINVAL;
+    if (npts > (int64_t)INT32_MAX) return INTERP_ESIZE;
+    const int s = h->s;
+    // bins of 2^bb padded cells per axis; Morton keys of `bits` bits per axis, at most 2^22 keys
+    int bb = s == 3 ? 2 : 1, bits = 0;
+    for (;;) {
+        int maxnb = 1;
+        for (int a = 0; a < s; ++a) maxnb = std::max(maxnb, (h->lay32.pdims[a] + (1 << bb) - 1) >> bb);
+        bits = 0;
+        while ((1 << bits) < maxnb) ++bits;
+        if (bits * s <= 22) break;
+        ++bb;
+    }
+    const int nkeys = 1 << (bits * s);
+    cudaError_t e = cudaSuccess;
+    if (h->sort_nkeys < nkeys) {
+        cudaFree(h->sort_keys);
+        h->sort_keys = nullptr;
+        h->sort_nkeys = 0;
+        e = cudaMalloc(&h->sort_keys, (size_t)nkeys * sizeof(unsigned));
+        if (e != cudaSuccess) {
+            h->sort_keys = nullptr;
+            cudaGetLastError();
+            return cuda_status(e);
+        }
+        h->sort_nkeys = nkeys;
+    }
+    e = h->ops->sort(pts, npts, h->lay32, bb, bits, h->sort_keys, nkeys, perm, pts_sorted,
+                     static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) cudaGetLastError();
     return cuda_status(e);
 }

@@ -804,3 +804,262 @@ __global__ void __launch_bounds__(NT) k_eval_binned(const float *__restrict__ pt
 }
 
 }  // namespace ib
+
+// ------------------------------------------------------------------------------------ spatial sort
+
+namespace ib {
+
+// Bin of a query for the spatial sort: the padded cell index of coset 0, clamped to the array,
+// divided by 2^BB per axis, the bin coordinates interleaved bit by bit (Morton / Z order), so
+// queries that are close in space get close keys and a run of sorted queries covers a compact box.
+template <class SP>
+__device__ __forceinline__ unsigned sort_key(const float (&x)[SP::S], const ibl::Layout &L, int bb, int bits)
+{
+    constexpr int S = SP::S;
+    unsigned bin[S];
+    sfor<S>([&](auto A) {
+        constexpr int a = decltype(A)::value;
+        int i;
+        float y;
+        reduce_axis<SP::D, SP::COSET[0][a]>(x[a], i, y);
+        int P = i + L.pad;
+        P = P < 0 ? 0 : (P > L.pdims[a] - 1 ? L.pdims[a] - 1 : P);
+        bin[a] = (unsigned)P >> bb;
+    });
+    unsigned key = 0;
+    for (int b = 0; b < bits; ++b)
+        sfor<S>([&](auto A) { key |= ((bin[A] >> b) & 1u) << (b * S + A); });
+    return key;
+}
+
+// in-place exclusive prefix sum of n counters, one CTA of NT threads (n up to a few million);
+// a template so that every translation unit including this header has its own copy
+template <int NT>
+__global__ void __launch_bounds__(NT) k_scan_exclusive(unsigned *__restrict__ a, int n)
+{
+    static_assert(NT == 1024, "one CTA of 1024 threads");
+    __shared__ unsigned part[1024];
+    const int per = (n + 1023) / 1024;
+    const int beg = threadIdx.x * per;
+    const int end = beg + per < n ? beg + per : n;
+    unsigned s = 0;
+    for (int i = beg; i < end; ++i) s += a[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {          // inclusive Hillis-Steele scan
+        const unsigned v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+    for (int i = beg; i < end; ++i) {
+        const unsigned t = a[i];
+        a[i] = run;
+        run += t;
+    }
+}
+
+template <class SP>
+__global__ void k_sort_count(const float *__restrict__ pts, int64_t n, ibl::Layout L, int bb, int bits,
+                             unsigned *__restrict__ counts)
+{
+    constexpr int S = SP::S;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        float x[S];
+        sfor<S>([&](auto A) {
+            const float v = pts[q * S + A];
+            x[A] = isfinite(v) ? v : 0.0f;             // non-finite queries go to some bin
+        });
+        atomicAdd(&counts[sort_key<SP>(x, L, bb, bits)], 1u);
+    }
+}
+
+template <class SP>
+__global__ void k_sort_scatter(const float *__restrict__ pts, int64_t n, ibl::Layout L, int bb, int bits,
+                               unsigned *__restrict__ cursor, int32_t *__restrict__ perm, float *__restrict__ pts_out)
+{
+    constexpr int S = SP::S;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        float x[S], xr[S];
+        sfor<S>([&](auto A) {
+            xr[A] = pts[q * S + A];
+            x[A] = isfinite(xr[A]) ? xr[A] : 0.0f;
+        });
+        const unsigned pos = atomicAdd(&cursor[sort_key<SP>(x, L, bb, bits)], 1u);
+        if (perm) perm[pos] = (int32_t)q;
+        if (pts_out) sfor<S>([&](auto A) { pts_out[(int64_t)pos * S + A] = xr[A]; });
+    }
+}
+
+// ------------------------------------------------------------------------------------ privatised adjoint
+
+// w_site = sum_mon A[mon][site] mu[mon]; at the last nonzero of a site, add it to the CTA's
+// shared-memory copy of the box around its queries (local linear offsets)
+template <class SP, int J, int NM, int SITE, int MON, float VAL, int FIRST, int SF, int SL>
+__device__ __forceinline__ void nz_scatter_local(const float (&mu)[NM], float &acc, const int (&lss)[SP::S], int lbase,
+                                                 float *sacc, interp_gen::nz<SITE, MON, VAL, FIRST, SF, SL>)
+{
+    if constexpr (SF) acc = mu[MON] * VAL;
+    else acc = fmaf(mu[MON], VAL, acc);
+    if constexpr (SL) {
+        int off = lbase;
+        sfor<SP::S>([&](auto A) {
+            constexpr int g = SP::SITE[J][SITE][decltype(A)::value];
+            if constexpr (g != 0) off += g * lss[A];
+        });
+        atomicAdd(sacc + off, acc);
+    }
+}
+template <class SP, int J, int NM, class... Z>
+__device__ __forceinline__ void scatter_local_all(const float (&mu)[NM], const int (&lss)[SP::S], int lbase, float *sacc,
+                                                  interp_gen::nzlist<Z...>)
+{
+    float acc = 0.0f;
+    (nz_scatter_local<SP, J, NM>(mu, acc, lss, lbase, sacc, Z{}), ...);
+}
+
+template <class SP, int J>
+__device__ __forceinline__ void adjoint_piece_local(const Fold<SP::S> &f, const int (&lss)[SP::S], int lbase,
+                                                    float *sacc, float w)
+{
+    constexpr int S = SP::S;
+    constexpr int NM = SP::NMON;
+    float t[S];
+    sfor<S>([&](auto A) {
+        constexpr float an = SP::ANCHOR[J][decltype(A)::value];
+        t[A] = f.t[A] - an;
+    });
+    float mu[NM];
+    monomials<S, S, SP::DEG, 0, NM>(mu, t, w);
+    scatter_local_all<SP, J, NM>(mu, lss, lbase, sacc, typename SP::template NZL<J>{});
+}
+
+// Adjoint over chunks of CH queries per CTA.  Each CTA first finds the padded-cell bounding box
+// of its queries (all cosets); if the box plus the stencil halo fits in shared memory -- it does
+// when the queries are sorted spatially -- the contributions are summed there with shared-memory
+// atomics and added to the global buffer once per site; otherwise every contribution goes
+// straight to the global buffer (unsorted queries).
+constexpr int kAdjChunk = 1024;
+constexpr int kAdjSmemFloats = 6144;
+
+template <class SP>
+__global__ void __launch_bounds__(256, 2) k_adjoint_priv(const float *__restrict__ pts, int64_t n,
+                                                      const float *__restrict__ gout, DevVol<float> v,
+                                                      float *__restrict__ dpad)
+{
+    constexpr int S = SP::S, M = SP::M, H = SP::HALO;
+    __shared__ float sacc[kAdjSmemFloats];
+    __shared__ int bmin[S], bmax[S];
+    const int64_t c0 = (int64_t)blockIdx.x * kAdjChunk;
+    const int64_t c1 = c0 + kAdjChunk < n ? c0 + kAdjChunk : n;
+    if (threadIdx.x < S) {
+        bmin[threadIdx.x] = 0x7fffffff;
+        bmax[threadIdx.x] = -0x7fffffff;
+    }
+    __syncthreads();
+    // pass 1: bounding box of the padded cell indices (every coset) of the chunk's live queries
+    for (int64_t q = c0 + threadIdx.x; q < c1; q += blockDim.x) {
+        float x[S];
+        bool ok = gout[q] != 0.0f;
+        sfor<S>([&](auto A) {
+            x[A] = pts[q * S + A];
+            ok &= isfinite(x[A]);
+        });
+        if (!ok) continue;
+        sfor<M>([&](auto Kc) {
+            constexpr int K = decltype(Kc)::value;
+            int P[S];
+            bool in = true;
+            sfor<S>([&](auto A) {
+                constexpr int a = decltype(A)::value;
+                float y;
+                int i;
+                reduce_axis<SP::D, SP::COSET[K][a]>(x[a], i, y);
+                in &= (unsigned)(i + H) < (unsigned)(v.L.n[a] + 2 * H);
+                P[a] = i + 2 * H;
+            });
+            if (in)
+                sfor<S>([&](auto A) {
+                    atomicMin(&bmin[A], P[A]);
+                    atomicMax(&bmax[A], P[A]);
+                });
+        });
+    }
+    __syncthreads();
+    int ld[S], lstride[S];
+    int vol = 1;
+    bool empty = false;
+    for (int a = S - 1; a >= 0; --a) {
+        empty |= bmax[a] < bmin[a];
+        ld[a] = bmax[a] - bmin[a] + 1 + 2 * H;
+        lstride[a] = vol;
+        vol = (vol < (1 << 24) && ld[a] > 0) ? vol * ld[a] : (1 << 24);
+    }
+    if (empty) return;
+    const bool priv = (int64_t)vol * M <= kAdjSmemFloats;
+    if (priv) {
+        for (int i = threadIdx.x; i < vol * M; i += blockDim.x) sacc[i] = 0.0f;
+        __syncthreads();
+    }
+    // pass 2: the contributions
+    for (int64_t q = c0 + threadIdx.x; q < c1; q += blockDim.x) {
+        float x[S];
+        bool finite = true;
+        sfor<S>([&](auto A) {
+            x[A] = pts[q * S + A];
+            finite &= isfinite(x[A]);
+        });
+        const float w = gout[q];
+        if (!finite || w == 0.0f) continue;
+        sfor<M>([&](auto Kc) {
+            constexpr int K = decltype(Kc)::value;
+            const auto f = fold_coset<SP, K, float>(x, v);
+            if (!f.in_range) return;
+            if (priv) {
+                // local offset of the cell's site and signed local strides per folded slot
+                int P[S];
+                sfor<S>([&](auto A) {
+                    constexpr int a = decltype(A)::value;
+                    float y;
+                    int i;
+                    reduce_axis<SP::D, SP::COSET[K][a]>(x[a], i, y);
+                    P[a] = i + 2 * H;
+                });
+                int lbase = K * vol, lss[S];
+                sfor<S>([&](auto A) {
+                    lbase += (P[A] - bmin[A] + H) * lstride[A];
+                    int st = lstride[0];
+                    sfor<S - 1>([&](auto B) {
+                        if (f.sl[A].ax == 1 + decltype(B)::value) st = lstride[1 + decltype(B)::value];
+                    });
+                    lss[A] = f.sl[A].sg * st;
+                });
+                sfor<SP::K>([&](auto Jc) {
+                    if (f.piece == decltype(Jc)::value) adjoint_piece_local<SP, decltype(Jc)::value>(f, lss, lbase, sacc, w);
+                });
+            } else {
+                sfor<SP::K>([&](auto Jc) {
+                    if (f.piece == decltype(Jc)::value) adjoint_piece<SP, decltype(Jc)::value>(f, dpad, w);
+                });
+            }
+        });
+    }
+    if (!priv) return;
+    __syncthreads();
+    // pass 3: add the shared box to the global padded buffer, one atomic per touched site
+    for (int i = threadIdx.x; i < vol * M; i += blockDim.x) {
+        const float a = sacc[i];
+        if (a == 0.0f) continue;
+        int r = i, p[S];
+        const int k = r / vol;
+        r -= k * vol;
+        for (int ax = S - 1; ax >= 0; --ax) {
+            p[ax] = r % ld[ax] + bmin[ax] - H;
+            r /= ld[ax];
+        }
+        atomicAdd(dpad + ibl::elem_offset(v.L, k, p), a);
+    }
+}
+
+}  // namespace ib

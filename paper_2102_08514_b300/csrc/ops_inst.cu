@@ -1,6 +1,7 @@
 // ops_inst.cu -- instantiates the kernels of ONE spline and ONE kernel family.  The build
 // compiles this file once per (spline, family) with -DINTERP_SPLINE=<name> -DINTERP_PART=<0..3>
 // so the large unrolled kernels compile in parallel.
+#include <algorithm>
 #include <cstdlib>
 
 #include "kernels.cuh"
@@ -78,7 +79,21 @@ cudaError_t launch_eval(const float *pts, int64_t n, const void *c, const ibl::L
 [[maybe_unused]] cudaError_t launch_adjoint(const float *pts, int64_t n, const float *gout, const ibl::Layout &L,
                                             float *dpad, cudaStream_t st)
 {
-    ib::k_adjoint<SP><<<grid_for(n), kTPB, 0, st>>>(pts, n, gout, make_vol<float>(nullptr, L), dpad);
+    const unsigned grid = (unsigned)((n + ib::kAdjChunk - 1) / ib::kAdjChunk);
+    ib::k_adjoint_priv<SP><<<grid, 256, 0, st>>>(pts, n, gout, make_vol<float>(nullptr, L), dpad);
+    return cudaPeekAtLastError();
+}
+
+// counting sort of the queries by Morton-ordered bins: count, exclusive scan, scatter
+[[maybe_unused]] cudaError_t launch_sort(const float *pts, int64_t n, const ibl::Layout &L, int bb, int bits,
+                                         unsigned *keys, int nkeys, int32_t *perm, float *pts_out, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(keys, 0, (size_t)nkeys * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 148 * 16);
+    ib::k_sort_count<SP><<<grid, 256, 0, st>>>(pts, n, L, bb, bits, keys);
+    ib::k_scan_exclusive<1024><<<1, 1024, 0, st>>>(keys, nkeys);
+    ib::k_sort_scatter<SP><<<grid, 256, 0, st>>>(pts, n, L, bb, bits, keys, perm, pts_out);
     return cudaPeekAtLastError();
 }
 
@@ -126,6 +141,7 @@ void IB_CAT(fill_, INTERP_SPLINE, _, INTERP_PART)(SplineOps &o)
     o.lookups = SP::LOOKUPS;
     o.adjoint = launch_adjoint;
     o.debug = launch_debug;
+    o.sort = launch_sort;
     if constexpr (SP::S == 3) {
         o.rays[0] = launch_rays<false>;
         o.rays[1] = launch_rays<true>;

@@ -13,6 +13,8 @@ using EvalFn = cudaError_t (*)(const float *, int64_t, const void *, const ibl::
                                const float *, cudaStream_t);
 using AdjFn = cudaError_t (*)(const float *, int64_t, const float *, const ibl::Layout &, float *, cudaStream_t);
 using RayFn = cudaError_t (*)(const ibl::RayGeom &, const void *, const ibl::Layout &, float *, float *, cudaStream_t);
+using SortFn = cudaError_t (*)(const float *, int64_t, const ibl::Layout &, int, int, unsigned *, int, int32_t *,
+                               float *, cudaStream_t);
 using DbgFn = cudaError_t (*)(const float *, int64_t, const ibl::Layout &, int32_t *, int32_t *, cudaStream_t);
 
 struct SplineOps {
@@ -26,6 +28,7 @@ struct SplineOps {
     AdjFn adjoint = nullptr;
     RayFn rays[2] = {};          // [value, value+grad], 3-D splines, FP32 storage
     DbgFn debug = nullptr;
+    SortFn sort = nullptr;
 };
 
 // kernel families, one translation unit each

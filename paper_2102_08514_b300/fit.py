@@ -17,9 +17,15 @@ def mse_loss(f, y):
 
 
 def fit(interp: Interpolator, pts, targets, steps: int = 200, lr: float = 0.05, betas=(0.9, 0.999),
-        eps: float = 1e-8, coeffs=None, record_every: int = 1):
-    """Adam on the coefficients (start: zeros, or `coeffs`).  Returns (coefficients, losses)."""
+        eps: float = 1e-8, coeffs=None, record_every: int = 1, sort: bool = True):
+    """Adam on the coefficients (start: zeros, or `coeffs`).  Returns (coefficients, losses).
+
+    With sort=True the samples are reordered once by interp_sort_points (the loss does not
+    depend on their order); every evaluation and adjoint then runs on spatially sorted queries."""
     import torch
+    if sort:
+        perm, pts = interp.sort_points(pts)
+        targets = targets[perm.long()]
     c = (torch.zeros(interp.shape, device=pts.device, dtype=torch.float32) if coeffs is None
          else coeffs.detach().clone().float()).requires_grad_(True)
     opt = torch.optim.Adam([c], lr=lr, betas=betas, eps=eps)
