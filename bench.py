@@ -265,27 +265,58 @@ def time_fit_step(torch, itp, wl, pts, pts_h, steps, warmup, stream, barrier):
     return statistics.mean(per)
 
 
+class Ranks:
+    """The multi-process harness: one process per GPU (torchrun), independent query shards (weak
+    scaling, no data-path collective), a barrier around the timed region and the step time taken
+    as the max over ranks.  backend "nccl" on GPUs; "gloo" runs the same logic on CPU (tests)."""
+
+    def __init__(self, backend: str = "nccl"):
+        import torch
+        import torch.distributed as dist
+        self.dist = dist
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.device = "cpu"
+        if self.world > 1:
+            if backend == "nccl":
+                torch.cuda.set_device(self.local)
+                self.device = f"cuda:{self.local}"
+                dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+            else:
+                dist.init_process_group(backend)
+
+    def query_seed(self, base: int) -> int:
+        """Each rank draws its own queries."""
+        return base + 1000 * self.rank
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def max_over_ranks(self, x: float) -> float:
+        if self.world == 1:
+            return x
+        import torch
+        t = torch.tensor([x], device=self.device, dtype=torch.float64)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def job_throughput(self, per_rank_units: int, max_ms: float) -> float:
+        """Units processed by all ranks / the slowest rank's time."""
+        return self.world * per_rank_units / (max_ms * 1e-3)
+
+    def close(self):
+        if self.world > 1:
+            self.dist.destroy_process_group()
+
+
 def run_ours(args):
     import torch
-    import torch.distributed as dist
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    rk = Ranks("nccl")
+    rank, world = rk.rank, rk.world
+    barrier, max_over_ranks = rk.barrier, rk.max_over_ranks
 
     from paper_2102_08514_b300.binding import Interpolator
 
@@ -300,7 +331,7 @@ def run_ours(args):
     itp.set_coeffs(torch.from_numpy(c).to(tdt).cuda())
     lo, hi = interior_box(wl.spline, wl.dims)
     n = args.queries or wl.queries
-    pts_h = uniform_points(make_rng(wl.seed + 1000 * rank, 0), n, lo, hi)
+    pts_h = uniform_points(make_rng(rk.query_seed(wl.seed), 0), n, lo, hi)
     pts = torch.from_numpy(pts_h).cuda()
     out = torch.empty(n, device="cuda")
     grad = torch.empty(n, s, device="cuda")
@@ -318,7 +349,7 @@ def run_ours(args):
     clocks = clk.summary()
     total_ms = max_over_ranks(total_ms)
     ms_step = total_ms / args.steps
-    value = world * n / (ms_step * 1e-3)
+    value = rk.job_throughput(n, ms_step)
 
     # every form, same timing rules (the timed step above is one of them)
     fw = max(args.warmup, 3)
@@ -435,8 +466,7 @@ def run_ours(args):
             line["accuracy"] = acc
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    rk.close()
 
 
 # ----------------------------------------------------------------------------- the oracle (CPU)

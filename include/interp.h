@@ -140,9 +140,10 @@ interp_status interp_eval_host(interp_t *h, const float *pts, int64_t npts, floa
  * dcoeffs has the coefficient layout of interp_set_coeffs (FP32) and is ACCUMULATED into: zero it
  * first for a plain gradient.  The scatter uses FP32 atomics into a handle-owned padded buffer,
  * so the order of additions, and the last bits of dcoeffs, vary between runs.  dcoeffs may be
- * NULL to compute dpts only.  Each block of 1024 consecutive queries whose cells fit a small box
- * (e.g. after interp_sort_points) is summed in shared memory first, with one global atomic per
- * touched coefficient; other blocks add every contribution with its own atomic.
+ * NULL to compute dpts only.  3-D splines: each block of 1024 consecutive queries whose cells fit
+ * a small box (e.g. after interp_sort_points) is summed in shared memory first, with one global
+ * atomic per touched coefficient; other blocks (and 4-D splines) add every contribution with its
+ * own atomic.
  */
 interp_status interp_backward(interp_t *h, const float *pts, int64_t npts, const float *gout, float *dcoeffs,
                               float *dpts, void *stream);

@@ -605,20 +605,36 @@ static void adj_fn(void *vctx, int k, int64_t lin, double phi, const double *gph
     ctx->d[lin] += ctx->g * phi;
 }
 
-/* dcoeffs[n] += sum_q g_q phi(x_q - n)  (single-threaded: the sum order is the query order) */
+/* dcoeffs[n] += sum_q g_q phi(x_q - n).  Each thread sums its share of the queries into its own
+ * array; the arrays are then added into dcoeffs. */
 int orc_adjoint(void *h, int D, int M, const int *lk, const int *dims, int64_t npts,
                 const double *pts, const double *g, double *dcoeffs)
 {
     orc_spline *sp = (orc_spline *)h;
     orc_layout ly = {D, M, lk, dims};
-    orc_memo mm;
-    if (memo_init(&mm, sp)) return ORC_ENOMEM;
+    int64_t total = M;
+    for (int a = 0; a < sp->s; ++a) total *= dims[a];
     int err = 0;
-    for (int64_t q = 0; q < npts && !err; ++q) {
-        adj_ctx ctx = {dcoeffs, g[q]};
-        err = for_each_site(sp, &mm, &ly, pts + q * sp->s, 0, adj_fn, &ctx);
+#pragma omp parallel
+    {
+        orc_memo mm;
+        int lerr = memo_init(&mm, sp);
+        double *mine = (double *)calloc((size_t)total, sizeof(double));
+        if (!mine) lerr = ORC_ENOMEM;
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t q = 0; q < npts; ++q) {
+            if (lerr) continue;
+            adj_ctx ctx = {mine, g[q]};
+            lerr = for_each_site(sp, &mm, &ly, pts + q * sp->s, 0, adj_fn, &ctx);
+        }
+#pragma omp critical
+        {
+            if (lerr) err = lerr;
+            else for (int64_t i = 0; i < total; ++i) dcoeffs[i] += mine[i];
+        }
+        free(mine);
+        memo_free(&mm);
     }
-    memo_free(&mm);
     return err;
 }
 

@@ -628,7 +628,8 @@ interp_status interp_sort_points(interp_t *h, const float *pts, int64_t npts, in
         cudaFree(h->sort_keys);
         h->sort_keys = nullptr;
         h->sort_nkeys = 0;
-        e = cudaMalloc(&h->sort_keys, (size_t)nkeys * sizeof(unsigned));
+        // the counters, then one partial sum per 4096 counters for the scan
+        e = cudaMalloc(&h->sort_keys, ((size_t)nkeys + nkeys / 4096 + 1) * sizeof(unsigned));
         if (e != cudaSuccess) {
             h->sort_keys = nullptr;
             cudaGetLastError();

@@ -860,6 +860,59 @@ __global__ void __launch_bounds__(NT) k_scan_exclusive(unsigned *__restrict__ a,
     }
 }
 
+// Parallel exclusive prefix sum of n counters in three launches: per-block sums of 4096
+// elements, an exclusive scan of those sums (k_scan_exclusive, one CTA), then a scan of every
+// block offset by its sum.  Templates, like k_scan_exclusive, so every unit has its own copy.
+constexpr int kScanBlock = 4096;
+
+template <int NT>
+__device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned *part, unsigned &total)
+{
+    part[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < NT; off <<= 1) {
+        const unsigned u = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += u;
+        __syncthreads();
+    }
+    total = part[NT - 1];
+    const unsigned ex = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+    __syncthreads();
+    return ex;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_scan_block_sums(const unsigned *__restrict__ a, int n, unsigned *__restrict__ sums)
+{
+    static_assert(NT * 4 == kScanBlock, "4 elements per thread");
+    __shared__ unsigned part[NT];
+    const int base = blockIdx.x * kScanBlock + threadIdx.x * 4;
+    unsigned v = 0;
+    for (int i = 0; i < 4; ++i) v += base + i < n ? a[base + i] : 0u;
+    unsigned total;
+    block_exclusive_scan<NT>(v, part, total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_scan_apply(unsigned *__restrict__ a, int n, const unsigned *__restrict__ sums)
+{
+    __shared__ unsigned part[NT];
+    const int base = blockIdx.x * kScanBlock + threadIdx.x * 4;
+    unsigned v[4], s = 0;
+    for (int i = 0; i < 4; ++i) {
+        v[i] = base + i < n ? a[base + i] : 0u;
+        s += v[i];
+    }
+    unsigned total;
+    unsigned run = block_exclusive_scan<NT>(s, part, total) + sums[blockIdx.x];
+    for (int i = 0; i < 4; ++i) {
+        if (base + i < n) a[base + i] = run;
+        run += v[i];
+    }
+}
+
 template <class SP>
 __global__ void k_sort_count(const float *__restrict__ pts, int64_t n, ibl::Layout L, int bb, int bits,
                              unsigned *__restrict__ counts)

@@ -79,8 +79,14 @@ cudaError_t launch_eval(const float *pts, int64_t n, const void *c, const ibl::L
 [[maybe_unused]] cudaError_t launch_adjoint(const float *pts, int64_t n, const float *gout, const ibl::Layout &L,
                                             float *dpad, cudaStream_t st)
 {
-    const unsigned grid = (unsigned)((n + ib::kAdjChunk - 1) / ib::kAdjChunk);
-    ib::k_adjoint_priv<SP><<<grid, 256, 0, st>>>(pts, n, gout, make_vol<float>(nullptr, L), dpad);
+    if constexpr (SP::S == 3) {
+        // blocks of sorted queries fit a shared-memory box: privatised sums (3-D)
+        const unsigned grid = (unsigned)((n + ib::kAdjChunk - 1) / ib::kAdjChunk);
+        ib::k_adjoint_priv<SP><<<grid, 256, 0, st>>>(pts, n, gout, make_vol<float>(nullptr, L), dpad);
+    } else {
+        // a 4-D box with its stencil halo does not fit shared memory: direct atomics
+        ib::k_adjoint<SP><<<grid_for(n), kTPB, 0, st>>>(pts, n, gout, make_vol<float>(nullptr, L), dpad);
+    }
     return cudaPeekAtLastError();
 }
 
@@ -92,7 +98,12 @@ cudaError_t launch_eval(const float *pts, int64_t n, const void *c, const ibl::L
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 148 * 16);
     ib::k_sort_count<SP><<<grid, 256, 0, st>>>(pts, n, L, bb, bits, keys);
-    ib::k_scan_exclusive<1024><<<1, 1024, 0, st>>>(keys, nkeys);
+    // exclusive scan of the counters; the block sums live right after them
+    const int nblk = (nkeys + ib::kScanBlock - 1) / ib::kScanBlock;
+    unsigned *sums = keys + nkeys;
+    ib::k_scan_block_sums<1024><<<nblk, 1024, 0, st>>>(keys, nkeys, sums);
+    ib::k_scan_exclusive<1024><<<1, 1024, 0, st>>>(sums, nblk);
+    ib::k_scan_apply<1024><<<nblk, 1024, 0, st>>>(keys, nkeys, sums);
     ib::k_sort_scatter<SP><<<grid, 256, 0, st>>>(pts, n, L, bb, bits, keys, perm, pts_out);
     return cudaPeekAtLastError();
 }
