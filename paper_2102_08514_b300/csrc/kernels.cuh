@@ -690,28 +690,15 @@ constexpr size_t binned_smem_bytes()
     return (size_t)NI * (sizeof(BinRec<SP::S>) + NV * sizeof(float) + 2 * sizeof(unsigned short) + 1) + 64;
 }
 
-// T queries per tile, NT threads per CTA.  With NT = 512 and a large tile the CTA fills an SM,
-// and its warps walk through the sorted pieces together, so only one or two pieces' code is hot
-// in the instruction caches at a time.
-template <class SP, class CT, int MODE, int T, int NT>
-__global__ void __launch_bounds__(NT) k_eval_binned(const float *__restrict__ pts, int64_t n, DevVol<CT> v,
-                                                    float *__restrict__ out, float *__restrict__ grad,
-                                                    const float *__restrict__ gout)
+// classify the tile's (query, coset) items and counting-sort them by piece in shared memory:
+// on return perm[0 .. start[K]) lists the live items in piece order (ends with a barrier)
+template <class SP, class CT, int T>
+__device__ __forceinline__ void bin_tile(const float *__restrict__ pts, int64_t n, const DevVol<CT> &v, int64_t q0,
+                                         BinRec<SP::S> *rec, unsigned short *perm, unsigned short *rank,
+                                         signed char *rpiece, int *cnt, int *start)
 {
     constexpr int S = SP::S, M = SP::M, K = SP::K, NI = T * M;
-    constexpr bool GRAD = MODE != 0;
-    constexpr int NV = GRAD ? S + 1 : 1;            // value (and gradient) per item
-    static_assert(NI <= 65535, "item index must fit 16 bits");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    BinRec<S> *rec = reinterpret_cast<BinRec<S> *>(smem_raw);
-    float *acc = reinterpret_cast<float *>(rec + NI);
-    unsigned short *perm = reinterpret_cast<unsigned short *>(acc + NI * NV);
-    unsigned short *rank = perm + NI;
-    signed char *rpiece = reinterpret_cast<signed char *>(rank + NI);
-    __shared__ int cnt[K], start[K + 1];
     const int tid = threadIdx.x;
-    const int64_t q0 = (int64_t)blockIdx.x * T;
-    for (int i = tid; i < NI * NV; i += blockDim.x) acc[i] = 0.0f;
     if (tid < K) cnt[tid] = 0;
     __syncthreads();
     // classify: item i = (query q0 + i % T, coset i / T)
@@ -759,6 +746,31 @@ __global__ void __launch_bounds__(NT) k_eval_binned(const float *__restrict__ pt
     for (int i = tid; i < NI; i += blockDim.x)
         if (rpiece[i] >= 0) perm[start[rpiece[i]] + rank[i]] = (unsigned short)i;
     __syncthreads();
+}
+
+// T queries per tile, NT threads per CTA.  With NT = 512 and a large tile the CTA fills an SM,
+// and its warps walk through the sorted pieces together, so only one or two pieces' code is hot
+// in the instruction caches at a time.
+template <class SP, class CT, int MODE, int T, int NT>
+__global__ void __launch_bounds__(NT) k_eval_binned(const float *__restrict__ pts, int64_t n, DevVol<CT> v,
+                                                    float *__restrict__ out, float *__restrict__ grad,
+                                                    const float *__restrict__ gout)
+{
+    constexpr int S = SP::S, M = SP::M, K = SP::K, NI = T * M;
+    constexpr bool GRAD = MODE != 0;
+    constexpr int NV = GRAD ? S + 1 : 1;            // value (and gradient) per item
+    static_assert(NI <= 65535, "item index must fit 16 bits");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    BinRec<S> *rec = reinterpret_cast<BinRec<S> *>(smem_raw);
+    float *acc = reinterpret_cast<float *>(rec + NI);
+    unsigned short *perm = reinterpret_cast<unsigned short *>(acc + NI * NV);
+    unsigned short *rank = perm + NI;
+    signed char *rpiece = reinterpret_cast<signed char *>(rank + NI);
+    __shared__ int cnt[K], start[K + 1];
+    const int tid = threadIdx.x;
+    const int64_t q0 = (int64_t)blockIdx.x * T;
+    for (int i = tid; i < NI * NV; i += blockDim.x) acc[i] = 0.0f;
+    bin_tile<SP, CT, T>(pts, n, v, q0, rec, perm, rank, rpiece, cnt, start);
     // evaluate in piece order: consecutive lanes take consecutive sorted items
     const int total = start[K];
     for (int p = tid; p < total; p += blockDim.x) {
@@ -801,6 +813,43 @@ __global__ void __launch_bounds__(NT) k_eval_binned(const float *__restrict__ pt
             sfor<S>([&](auto A) { grad[q * S + A] = w * g[A]; });
         }
     }
+}
+
+// adjoint of a multi-piece spline, piece-binned like k_eval_binned: after the sort each warp
+// scatters one piece's contributions (global atomics into the padded buffer)
+template <class SP, int T, int NT>
+__global__ void __launch_bounds__(NT) k_adjoint_binned(const float *__restrict__ pts, int64_t n,
+                                                       const float *__restrict__ gout, DevVol<float> v,
+                                                       float *__restrict__ dpad)
+{
+    constexpr int S = SP::S, M = SP::M, K = SP::K, NI = T * M;
+    static_assert(NI <= 65535, "item index must fit 16 bits");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    BinRec<S> *rec = reinterpret_cast<BinRec<S> *>(smem_raw);
+    unsigned short *perm = reinterpret_cast<unsigned short *>(rec + NI);
+    unsigned short *rank = perm + NI;
+    signed char *rpiece = reinterpret_cast<signed char *>(rank + NI);
+    __shared__ int cnt[K], start[K + 1];
+    const int64_t q0 = (int64_t)blockIdx.x * T;
+    bin_tile<SP, float, T>(pts, n, v, q0, rec, perm, rank, rpiece, cnt, start);
+    const int total = start[K];
+    for (int p = threadIdx.x; p < total; p += blockDim.x) {
+        const int i = perm[p];
+        const float w = gout[q0 + i % T];
+        if (w == 0.0f) continue;
+        const int j = rpiece[i];
+        const Fold<S> f = unpack_rec<SP, float>(rec[i], v);
+        sfor<K>([&](auto Jc) {
+            if (j == decltype(Jc)::value) adjoint_piece<SP, decltype(Jc)::value>(f, dpad, w);
+        });
+    }
+}
+
+template <class SP, int T>
+constexpr size_t binned_adjoint_smem_bytes()
+{
+    constexpr int NI = T * SP::M;
+    return (size_t)NI * (sizeof(BinRec<SP::S>) + 2 * sizeof(unsigned short) + 1) + 64;
 }
 
 }  // namespace ib

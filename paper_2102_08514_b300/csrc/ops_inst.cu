@@ -83,6 +83,21 @@ cudaError_t launch_eval(const float *pts, int64_t n, const void *c, const ibl::L
         // blocks of sorted queries fit a shared-memory box: privatised sums (3-D)
         const unsigned grid = (unsigned)((n + ib::kAdjChunk - 1) / ib::kAdjChunk);
         ib::k_adjoint_priv<SP><<<grid, 256, 0, st>>>(pts, n, gout, make_vol<float>(nullptr, L), dpad);
+    } else if constexpr (SP::K >= 4) {
+        // many pieces: sort each tile's items by piece first (no shared-memory box in 4-D)
+        constexpr int T = 1024, NT = 512;
+        constexpr size_t smem = ib::binned_adjoint_smem_bytes<SP, T>();
+        auto kern = ib::k_adjoint_binned<SP, T, NT>;
+        static unsigned long long configured = 0;
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev >= 64 || !(configured >> dev & 1ull)) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            if (dev < 64) configured |= 1ull << dev;
+        }
+        kern<<<(unsigned)((n + T - 1) / T), NT, smem, st>>>(pts, n, gout, make_vol<float>(nullptr, L), dpad);
     } else {
         // a 4-D box with its stencil halo does not fit shared memory: direct atomics
         ib::k_adjoint<SP><<<grid_for(n), kTPB, 0, st>>>(pts, n, gout, make_vol<float>(nullptr, L), dpad);
