@@ -20,6 +20,7 @@ workload (a deliberately slow baseline, not the target).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -311,6 +312,16 @@ class Ranks:
             self.dist.destroy_process_group()
 
 
+def workload_of(args):
+    """The workload named on the command line, with its spline replaced if --spline is given."""
+    wl = WORKLOADS[args.workload]
+    if args.spline and args.spline != wl.spline:
+        if len(LATTICES[SPLINES[args.spline].lattice].L) != len(wl.dims):
+            raise SystemExit(f"--spline {args.spline}: dimension differs from workload {wl.name}")
+        wl = dataclasses.replace(wl, spline=args.spline)
+    return wl
+
+
 def run_ours(args):
     import torch
 
@@ -320,7 +331,7 @@ def run_ours(args):
 
     from paper_2102_08514_b300.binding import Interpolator
 
-    wl = WORKLOADS[args.workload]
+    wl = workload_of(args)
     form = args.form or DEFAULT_FORM[wl.name]
     sp = SPLINES[wl.spline]
     lat = LATTICES[sp.lattice]
@@ -446,7 +457,7 @@ def run_ours(args):
     }
     line["forms"]["value"]["tflops"] = 2.0 * info.fma_value_per_query * n / (form_ms["value"] * 1e-3) / 1e12
     line["forms"]["value_grad"]["tflops"] = 2.0 * info.fma_grad_per_query * n / (form_ms["value_grad"] * 1e-3) / 1e12
-    if args.workload != WORKLOAD or args.storage != "f32" or form != DEFAULT_FORM[WORKLOAD]:
+    if args.workload != WORKLOAD or args.storage != "f32" or form != DEFAULT_FORM[WORKLOAD] or args.spline:
         line["metric"] = f"evals/s ({form}, {args.storage} storage)"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], (m, ref_v, ref_g) = cpu_baseline(wl, pts_h, c, form, seconds=args.cpu_seconds)
@@ -506,7 +517,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl = WORKLOADS[args.workload]
+    wl = workload_of(args)
     form = args.form or DEFAULT_FORM[wl.name]
     orc, spl, lat = _oracle_setup(wl)
     cores = os.cpu_count() or 1
@@ -536,7 +547,7 @@ def run_reference(args):
     dt = time.perf_counter() - t
     value = per_step * args.steps / dt
     line = {
-        "impl": "reference", "metric": METRIC if args.workload == WORKLOAD and form == DEFAULT_FORM[WORKLOAD]
+        "impl": "reference", "metric": METRIC if args.workload == WORKLOAD and form == DEFAULT_FORM[WORKLOAD] and not args.spline
         else f"evals/s ({form}, {args.storage} storage)", "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
@@ -560,6 +571,8 @@ def main():
     ap.add_argument("--form", choices=["value", "value_grad", "adjoint"], default=None)
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
     ap.add_argument("--queries", type=int, default=0, help="override the workload's query count")
+    ap.add_argument("--spline", choices=sorted(SPLINES), default=None,
+                    help="evaluate another spline of the same dimension on the workload's grid and queries")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

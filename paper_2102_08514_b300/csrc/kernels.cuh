@@ -336,13 +336,58 @@ __device__ __forceinline__ void eval_piece(const Fold<SP::S> &f, const DevVol<CT
         constexpr float an = SP::ANCHOR[J][decltype(A)::value];
         t[A] = f.t[A] - an;
     });
-    float b[NM];
-    sfor<NM>([&](auto A) { b[A] = 0.0f; });
-    accumulate<NS, NM>(b, c, typename SP::template NZL<J>{});
-    if constexpr (!GRAD) {
-        val += horner<S, S, SP::DEG, 0, NM>(b, t);
+    constexpr int DEG = SP::DEG;
+    VG<S> r;
+    if constexpr (NM > 120) {
+        // large monomial spaces: Horner in t_1 over blocks P_k(t_2..t_s) (k = DEG .. 0), block k's
+        // coefficients formed (b = A_j c restricted to the block) just before they are used
+        if constexpr (!GRAD) {
+            float acc = 0.0f;
+            sfor<DEG + 1>([&](auto I) {
+                constexpr int k = DEG - decltype(I)::value;
+                constexpr int NMB = nmon(S - 1, DEG - k);
+                float bb[NMB];
+                sfor<NMB>([&](auto Z) { bb[Z] = 0.0f; });
+                accumulate<NS, NMB>(bb, c, typename SP::template NZB<J, k>{});
+                const float inner = horner<S, S - 1, DEG - k, 0, NMB>(bb, t);
+                if constexpr (k == DEG) acc = inner;
+                else acc = fmaf(acc, t[0], inner);
+            });
+            val += acc;
+            return;
+        } else {
+            sfor<DEG + 1>([&](auto I) {
+                constexpr int k = DEG - decltype(I)::value;
+                constexpr int NMB = nmon(S - 1, DEG - k);
+                float bb[NMB];
+                sfor<NMB>([&](auto Z) { bb[Z] = 0.0f; });
+                accumulate<NS, NMB>(bb, c, typename SP::template NZB<J, k>{});
+                const VG<S - 1> p = horner_grad<S, S - 1, DEG - k, 0, NMB>(bb, t);
+                if constexpr (k == DEG) {
+                    r.v = p.v;
+                    r.g[0] = 0.0f;
+                    sfor<S - 1>([&](auto A) { r.g[1 + A] = p.g[A]; });
+                } else {
+                    if constexpr (k == DEG - 1) r.g[0] = r.v;        // d/dt_1 of the leading block
+                    else r.g[0] = fmaf(r.g[0], t[0], r.v);
+                    r.v = fmaf(r.v, t[0], p.v);
+                    sfor<S - 1>([&](auto A) { r.g[1 + A] = fmaf(r.g[1 + A], t[0], p.g[A]); });
+                }
+            });
+        }
     } else {
-        VG<S> r = horner_grad<S, S, SP::DEG, 0, NM>(b, t);
+        // b = A_j c for every monomial, then nested Horner
+        float b[NM];
+        sfor<NM>([&](auto A) { b[A] = 0.0f; });
+        accumulate<NS, NM>(b, c, typename SP::template NZL<J>{});
+        if constexpr (!GRAD) {
+            val += horner<S, S, DEG, 0, NM>(b, t);
+            return;
+        } else {
+            r = horner_grad<S, S, DEG, 0, NM>(b, t);
+        }
+    }
+    if constexpr (GRAD) {
         val += r.v;
         // back through the fold: d/dx_ax = sign * d/dy'_slot
         sfor<S>([&](auto A) {

@@ -26,12 +26,25 @@ def _twice(xi):
     return [row + row for row in xi]
 
 
+XI_I3 = [[1, 0, 0], [0, 1, 0], [0, 0, 1]]
+
+
+def _repeat(xi, k):
+    return [row * k for row in xi]
+
+
 CATALOG = {
     "bcc_linear": (L_BCC, XI_BCC_RD),
     "bcc_quintic": (L_BCC, _twice(XI_BCC_RD)),
     "fcc_6dir": (L_FCC, XI_FCC6),
     "cc_7dir": (L_CC, XI_CC7),
     "d4s_8dir": (L_D4S, XI_D4),
+    # the other Table 1 box splines
+    "bcc_quartic": (L_BCC, XI_BCC_QUARTIC),        # quartic truncated rhombic dodecahedron on BCC
+    "cc_linear_rd": (L_CC, XI_BCC_RD),             # linear rhombic dodecahedron on CC
+    "cc_voronoi1": (L_CC, _repeat(XI_I3, 2)),      # CC Voronoi spline 1 = trilinear B-spline
+    "cc_voronoi2": (L_CC, _repeat(XI_I3, 3)),      # CC Voronoi spline 2 = triquadratic B-spline
+    "cc_voronoi3": (L_CC, _repeat(XI_I3, 4)),      # CC Voronoi spline 3 = tricubic B-spline
 }
 
 

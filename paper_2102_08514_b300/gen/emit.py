@@ -25,7 +25,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 OUT_DIR = os.path.join(os.path.dirname(HERE), "csrc", "generated")
 # splines whose FP16 / BF16 coefficient-storage kernels are compiled (the 4-D spline's kernels are
 # large, so only its FP32 variant is built)
-HALF_STORAGE = {"bcc_linear", "bcc_quintic", "fcc_6dir", "cc_7dir"}
+HALF_STORAGE = {"bcc_linear", "bcc_quintic", "fcc_6dir", "cc_7dir", "bcc_quartic", "cc_linear_rd", "cc_voronoi1",
+                "cc_voronoi2", "cc_voronoi3"}
 
 
 def f32_hex(v) -> str:
@@ -127,6 +128,23 @@ def emit_struct(T, half_storage: bool = True) -> tuple[str, dict]:
         body = ",\n        ".join(", ".join(ents[i:i + 3]) for i in range(0, len(ents), 3))
         L.append(f"    using NZ{j} = nzlist<\n        {body}>;")
     L.append(f"    template <int J> using NZL = typename pick<J, {', '.join(f'NZ{j}' for j in range(K))}>::type;")
+    # the same nonzeros split by outer Horner block k (monomials t_1^k * (t_2..t_s)^beta), with
+    # monomial indices local to the block: NZB<J, k> drives the block-by-block evaluation
+    deg = T.degree
+    offs = [sum(n_monomials(s - 1, deg - kk) for kk in range(k)) for k in range(deg + 2)]
+    for j, z in enumerate(nz_lists):
+        blists = []
+        for k in range(deg + 1):
+            seen = set()
+            ents = []
+            for m, a, v in sorted(((m, a, v) for m, a, v in z if offs[k] <= a < offs[k + 1]), key=lambda e: (e[0], e[1])):
+                ents.append(f"nz<{m}, {a - offs[k]}, {f32_hex(v)}, {int(a not in seen)}, 0, 0>")
+                seen.add(a)
+            body = ",\n        ".join(", ".join(ents[i:i + 3]) for i in range(0, len(ents), 3))
+            L.append(f"    using NZB{j}_{k} = nzlist<{chr(10) + '        ' + body if ents else ''}>;")
+            blists.append(f"NZB{j}_{k}")
+        L.append(f"    using NZBL{j} = blocks<{', '.join(blists)}>;")
+    L.append(f"    template <int J, int B> using NZB = typename pick_block<B, typename pick<J, {', '.join(f'NZBL{j}' for j in range(K))}>::type>::type;")
     L.append(f"    static constexpr double FMA_VALUE = {fma_value!r}, FMA_GRAD = {fma_grad!r}, LOOKUPS = {lookups!r};")
     L.append("};")
 
@@ -173,6 +191,9 @@ def main(argv=None):
         "template <class... Z> struct nzlist { static constexpr int size = sizeof...(Z); };",
         "template <int J, class T0, class... Ts> struct pick { using type = typename pick<J - 1, Ts...>::type; };",
         "template <class T0, class... Ts> struct pick<0, T0, Ts...> { using type = T0; };",
+        "template <class... Bs> struct blocks {};",
+        "template <int K, class BL> struct pick_block;",
+        "template <int K, class... Bs> struct pick_block<K, blocks<Bs...>> { using type = typename pick<K, Bs...>::type; };",
         "",
         body,
         "",

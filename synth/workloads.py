@@ -64,6 +64,15 @@ SPLINES = {
                                                (1, 1, 1, 1, -1, -1, -1, -1),
                                                (1, 1, -1, -1, 1, 1, -1, -1),
                                                (1, -1, 1, -1, 1, -1, 1, -1))),
+    # Table 1: quartic truncated rhombic dodecahedron on BCC (7 directions)
+    "bcc_quartic": SplineSpec("bcc_quartic", "bcc", ((2, 0, 0, -1, 1, 1, -1), (0, 2, 0, 1, -1, 1, -1),
+                                                     (0, 0, 2, 1, 1, -1, -1))),
+    # Table 1: linear rhombic dodecahedron on CC
+    "cc_linear_rd": SplineSpec("cc_linear_rd", "cc", _BCC_RD),
+    # Table 1: CC Voronoi splines 1-3 (the identity directions repeated 2, 3, 4 times)
+    "cc_voronoi1": SplineSpec("cc_voronoi1", "cc", tuple(r * 2 for r in ((1, 0, 0), (0, 1, 0), (0, 0, 1)))),
+    "cc_voronoi2": SplineSpec("cc_voronoi2", "cc", tuple(r * 3 for r in ((1, 0, 0), (0, 1, 0), (0, 0, 1)))),
+    "cc_voronoi3": SplineSpec("cc_voronoi3", "cc", tuple(r * 4 for r in ((1, 0, 0), (0, 1, 0), (0, 0, 1)))),
 }
 
 

@@ -22,8 +22,11 @@ from synth import LATTICES, SPLINES
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 GEN = os.path.join(ROOT, "paper_2102_08514_b300", "csrc", "generated")
-NAMES = ["bcc_linear", "bcc_quintic", "fcc_6dir", "cc_7dir", "d4s_8dir"]
-TABLE1_LOOKUPS = {"bcc_linear": 4, "bcc_quintic": 32, "fcc_6dir": 16, "cc_7dir": 53, "d4s_8dir": 60}
+NAMES = ["bcc_linear", "bcc_quintic", "fcc_6dir", "cc_7dir", "d4s_8dir", "bcc_quartic", "cc_linear_rd", "cc_voronoi1",
+         "cc_voronoi2", "cc_voronoi3"]
+# Table 1 '# Lookups' (and Sec. 5.2 for D4*)
+TABLE1_LOOKUPS = {"bcc_linear": 4, "bcc_quintic": 32, "fcc_6dir": 16, "cc_7dir": 53, "d4s_8dir": 60, "bcc_quartic": 30,
+                  "cc_linear_rd": 16, "cc_voronoi1": 8, "cc_voronoi2": 27, "cc_voronoi3": 64}
 
 
 @pytest.fixture(scope="module")
@@ -78,7 +81,7 @@ def test_tables_match_the_oracle(tables, name):
     rng = np.random.default_rng(7)
     N = 6
     c = rng.uniform(-1, 1, (len(lat.cosets),) + (N,) * s)
-    npts = 40 if s == 4 else 80
+    npts = 40 if s == 4 or tab["degree"] > 6 else 80
     pts = (np.round(rng.uniform(0, lat.D * N, (npts, s)) * 2 ** 12) / 2 ** 12)
     ref = oracle.eval_sum(oracle.Spline(np.asarray(sp.xi), tab["det_l"]), lat.D, lat.cosets, c, pts)
     got = np.array([float(table_eval(tab, c, x)) for x in pts])

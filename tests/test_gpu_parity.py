@@ -17,10 +17,12 @@ from _gpu_common import VALUE_TOL, grad_bound, mixed_points, require_cuda, splin
 
 pytestmark = pytest.mark.gpu
 
-SPLINES_ALL = ["bcc_linear", "bcc_quintic", "fcc_6dir", "cc_7dir", "d4s_8dir"]
+SPLINES_ALL = ["bcc_linear", "bcc_quintic", "fcc_6dir", "cc_7dir", "d4s_8dir", "bcc_quartic", "cc_linear_rd",
+               "cc_voronoi1", "cc_voronoi2", "cc_voronoi3"]
 # small cases the oracle finishes in seconds, spanning several thread blocks and a ragged tail
 SMALL = {"bcc_linear": (12, 4133), "bcc_quintic": (12, 2085), "fcc_6dir": (10, 3011), "cc_7dir": (14, 2107),
-         "d4s_8dir": (7, 1093)}
+         "d4s_8dir": (7, 1093), "bcc_quartic": (12, 2091), "cc_linear_rd": (14, 3003), "cc_voronoi1": (14, 4099),
+         "cc_voronoi2": (14, 2049), "cc_voronoi3": (12, 389)}
 
 
 def _interp(name, dims, storage="f32"):
