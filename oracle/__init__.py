@@ -4,5 +4,5 @@ Only tests/, ``__graft_entry__.smoke()`` and the CPU-baseline / reference leg of
 import this package.  It shares no code with the CUDA product path.
 """
 from .oracle import (  # noqa: F401
-    Spline, build, lattice_sites, eval_sum, adjoint, cells, folded_offsets,
+    Spline, VoronoiSpline, build, lattice_sites, eval_sum, adjoint, cells, folded_offsets, zonotope_tiles,
 )

@@ -15,6 +15,9 @@ What it computes (Horacsek & Alim, arXiv 2102.08514):
 * ``adjoint``       -- dL/dc_k[i] = sum_q g_q phi(x_q - D i - l_k).
 * ``cells``         -- the exact shift rho to the region of evaluation (Sec. 4.1), here the cube
   [-D/2, D/2)^s centred on the nearest site of each coset.
+* ``VoronoiSpline`` -- the Voronoi splines V_n of Sec. 3 (the Voronoi region's indicator convolved
+  with itself), as the sum of shifted box splines Sec. 3 describes, each by the box-spline oracle;
+  its ``eval_sum`` / ``adjoint`` / ``phi`` mirror the functions above.
 """
 from __future__ import annotations
 
@@ -22,7 +25,8 @@ import ctypes
 import hashlib
 import os
 import subprocess
-from itertools import product
+from itertools import combinations, combinations_with_replacement, product
+from math import factorial
 
 import numpy as np
 
@@ -183,3 +187,145 @@ def folded_offsets(offsets: np.ndarray) -> np.ndarray:
     """Fold offsets into the chamber D/2 >= y_1 >= ... >= y_s >= 0 of the signed permutations
     (the reflection of Sec. 4.2 generalised to the full symmetry group of the cube)."""
     return -np.sort(-np.abs(offsets), axis=-1)
+
+
+# ----------------------------------------------------------------------------- Voronoi splines
+
+def _det3(m):
+    from fractions import Fraction as Fr
+    if len(m) == 1:
+        return Fr(m[0][0])
+    return sum((-1) ** j * m[0][j] * _det3([r[:j] + r[j + 1:] for r in m[1:]]) for j in range(len(m)))
+
+
+def _solve_exact(A, b):
+    """Cramer's rule over Fractions (A small and nonsingular)."""
+    d = _det3(A)
+    out = []
+    for j in range(len(A)):
+        Aj = [row[:j] + [b[i]] + row[j + 1:] for i, row in enumerate(A)]
+        out.append(_det3(Aj) / d)
+    return out
+
+
+def zonotope_tiles(gens, heights):
+    """Parallelepiped tiling of Z(G) = sum_j [0, g_j]: for every basis B of G, the offset z_B with
+    z_B + B[0,1)^s a tile.  It is the regular tiling of the heights h (one per generator, generic):
+    the tile of B projects the lower facet of the lifted zonotope spanned by the (g_b, h_b), which
+    contains the lifted g_j (j not in B) lying below the affine function through B's lifts.
+    Returns [(B, z_B, |det B|)]."""
+    from fractions import Fraction as Fr
+    s = len(gens[0])
+    out = []
+    for B in combinations(range(len(gens)), s):
+        rows = [[Fr(gens[b][a]) for a in range(s)] for b in B]       # g_b as rows
+        dB = _det3(rows)
+        if dB == 0:
+            continue
+        a_ = _solve_exact(rows, [Fr(heights[b]) for b in B])          # a . g_b = h_b
+        z = [Fr(0)] * s
+        for j, g in enumerate(gens):
+            if j in B:
+                continue
+            below = Fr(heights[j]) - sum(a_[k] * g[k] for k in range(s))
+            if below == 0:
+                raise ValueError("heights are not generic")
+            if below < 0:
+                z = [z[k] + g[k] for k in range(s)]
+        out.append((B, tuple(z), abs(dB)))
+    return out
+
+
+class VoronoiSpline:
+    """phi = |det L| V_n on the lattice L, with V_0 = chi (1/|det L| on the Voronoi region, here the
+    centred zonotope of the generators G) and V_n = V_0 * V_{n-1} (Sec. 3).
+
+    Following Sec. 3, V_0 is rewritten as a sum of constant box splines (the tiles z_B + B[0,1)^s of
+    the zonotope, each |det B| M_B), and the (n+1)-fold convolution is expanded by the multinomial
+    theorem; a convolution of box splines is the box spline of the concatenated directions,
+    shifted by the sum of the shifts.  Each term w M_{C}(x + c) is evaluated by the box-spline
+    oracle with the directions doubled (G is half-integral): M_C(y) = 2^s M_{2C}(2 y).
+    ``heights`` picks the tiling (any generic choice gives the same V_n).
+    """
+
+    def __init__(self, L, gens, order: int, heights=None):
+        from fractions import Fraction as Fr
+        L = np.asarray(L, dtype=np.int64)
+        self.s = L.shape[0]
+        self.det_l = abs(int(round(np.linalg.det(L))))
+        self.gens = [tuple(Fr(v) for v in g) for g in gens]
+        self.order = order
+        if heights is None:
+            heights = [Fr(2 * j * j + 3 * j + 5, 7 + j) for j in range(len(self.gens))]
+        self.tiles = zonotope_tiles(self.gens, heights)
+        s = self.s
+        ctr = [sum(g[a] for g in self.gens) / 2 for a in range(s)]
+        terms = {}
+        for combo in combinations_with_replacement(range(len(self.tiles)), order + 1):
+            mult = factorial(order + 1)
+            for i in set(combo):
+                mult //= factorial(combo.count(i))
+            w = Fr(mult) / Fr(self.det_l) ** order
+            for i in combo:
+                w *= self.tiles[i][2]
+            dirs = tuple(sorted(tuple(int(2 * v) for v in self.gens[b]) for i in combo for b in self.tiles[i][0]))
+            shift = tuple(sum(ctr[a] - self.tiles[i][1][a] for i in combo) for a in range(s))
+            terms[(dirs, shift)] = terms.get((dirs, shift), 0) + w
+        # group by direction multiset: one oracle Spline per group, (weight, doubled shift) list
+        self.groups = {}
+        for (dirs, shift), w in sorted(terms.items()):
+            xi2 = np.array(dirs, dtype=np.int64).T
+            # M_C(x + c) = 2^s M_{2C}(2x + 2c); the Spline is centred, so pass 2x + 2c - sum(2C)/2
+            d2 = np.array([float(2 * shift[a]) for a in range(s)]) - xi2.sum(axis=1) / 2.0
+            self.groups.setdefault(dirs, []).append((float(w) * 2 ** s, d2))
+        self.n_terms = len(terms)
+        self._splines = {dirs: Spline(np.array(dirs, dtype=np.int64).T, 1.0) for dirs in self.groups}
+
+    @property
+    def halfwidth(self) -> np.ndarray:
+        """Half-widths of the support's bounding box: (n+1) times the Voronoi region's."""
+        return (self.order + 1) * np.array([sum(abs(float(g[a])) for g in self.gens) / 2 for a in range(self.s)])
+
+    def phi(self, z, grad: bool = False):
+        """phi(z) (and grad) at points z (Q, s)."""
+        z = np.atleast_2d(np.asarray(z, dtype=np.float64))
+        out = np.zeros(z.shape[0])
+        g = np.zeros_like(z) if grad else None
+        for dirs, ws in self.groups.items():
+            sp = self._splines[dirs]
+            for w, d2 in ws:
+                r = sp.phi(2.0 * z + d2, grad=grad)
+                if grad:
+                    out += w * r[0]
+                    g += 2.0 * w * r[1]
+                else:
+                    out += w * r
+        return (out, g) if grad else out
+
+    def eval_sum(self, D: int, cosets, coeffs, points, grad: bool = False, nthreads: int = 0):
+        """f(x_q) = sum_k sum_i c_k[i] phi(x_q - D i - l_k) (and grad f) in FP64, brute force."""
+        p = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, self.s)
+        lk2 = 2 * np.asarray(cosets, dtype=np.int64).reshape(-1, self.s)
+        out = np.zeros(p.shape[0])
+        g = np.zeros_like(p) if grad else None
+        for dirs, ws in self.groups.items():
+            sp = self._splines[dirs]
+            for w, d2 in ws:
+                r = eval_sum(sp, 2 * D, lk2, coeffs, 2.0 * p + d2, grad=grad, nthreads=nthreads)
+                if grad:
+                    out += w * r[0]
+                    g += 2.0 * w * r[1]
+                else:
+                    out += w * r
+        return (out, g) if grad else out
+
+    def adjoint(self, D: int, cosets, shape, points, g) -> np.ndarray:
+        """dL/dc for dL/df = g: sum_q g_q phi(x_q - D i - l_k)."""
+        p = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, self.s)
+        lk2 = 2 * np.asarray(cosets, dtype=np.int64).reshape(-1, self.s)
+        d = np.zeros(shape)
+        for dirs, ws in self.groups.items():
+            sp = self._splines[dirs]
+            for w, d2 in ws:
+                d += w * adjoint(sp, 2 * D, lk2, shape, 2.0 * p + d2, g)
+        return d

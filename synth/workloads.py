@@ -32,7 +32,9 @@ class LatticeSpec:
 class SplineSpec:
     name: str
     lattice: str
-    xi: tuple         # s x n direction matrix (rows)
+    xi: tuple         # s x n direction matrix (rows); for a Voronoi spline, 2 G (see order)
+    order: int = 0    # 0: box spline M_xi; n >= 1: Voronoi spline V_n of the lattice, whose Voronoi
+                      # region is the centred zonotope of the generators G = xi / 2
 
 
 LATTICES = {
@@ -48,6 +50,8 @@ LATTICES = {
 }
 
 _BCC_RD = ((-1, 1, 1, -1), (1, -1, 1, -1), (1, 1, -1, -1))
+_BCC_VOR = ((1, 1, 1, 1, 0, 0), (1, -1, 0, 0, 1, 1), (0, 0, 1, -1, 1, -1))
+_FCC_VOR = ((1, 1, -1, -1), (1, -1, 1, -1), (1, -1, -1, 1))
 SPLINES = {
     # Table 1: linear rhombic dodecahedron on BCC (4 directions)
     "bcc_linear": SplineSpec("bcc_linear", "bcc", _BCC_RD),
@@ -73,6 +77,12 @@ SPLINES = {
     "cc_voronoi1": SplineSpec("cc_voronoi1", "cc", tuple(r * 2 for r in ((1, 0, 0), (0, 1, 0), (0, 0, 1)))),
     "cc_voronoi2": SplineSpec("cc_voronoi2", "cc", tuple(r * 3 for r in ((1, 0, 0), (0, 1, 0), (0, 0, 1)))),
     "cc_voronoi3": SplineSpec("cc_voronoi3", "cc", tuple(r * 4 for r in ((1, 0, 0), (0, 1, 0), (0, 0, 1)))),
+    # Table 1: Voronoi splines V_1, V_2 on BCC (truncated octahedron, six generators
+    # (+-1, +-1, 0) / 2) and on FCC (rhombic dodecahedron, four generators (+-1, +-1, +-1) / 2)
+    "bcc_voronoi1": SplineSpec("bcc_voronoi1", "bcc", _BCC_VOR, 1),
+    "bcc_voronoi2": SplineSpec("bcc_voronoi2", "bcc", _BCC_VOR, 2),
+    "fcc_voronoi1": SplineSpec("fcc_voronoi1", "fcc", _FCC_VOR, 1),
+    "fcc_voronoi2": SplineSpec("fcc_voronoi2", "fcc", _FCC_VOR, 2),
 }
 
 
@@ -85,7 +95,8 @@ def interior_box(spline: str, dims) -> tuple[np.ndarray, np.ndarray]:
     """Points strictly inside this box touch only stored coefficient sites (every coset)."""
     sp = SPLINES[spline]
     lat = LATTICES[sp.lattice]
-    h = support_halfwidth(sp.xi)
+    # a Voronoi spline V_n is supported on (n+1) times the Voronoi region, the zonotope of xi / 2
+    h = support_halfwidth(sp.xi) * ((sp.order + 1) / 2 if sp.order else 1)
     cos = np.asarray(lat.cosets)
     lo = cos.max(axis=0) + h - lat.D
     hi = cos.min(axis=0) + lat.D * np.asarray(dims) - h
