@@ -5,4 +5,5 @@ import this package.  It shares no code with the CUDA product path.
 """
 from .oracle import (  # noqa: F401
     Spline, VoronoiSpline, build, lattice_sites, eval_sum, adjoint, cells, folded_offsets, zonotope_tiles,
+    prefilter, d4_quasi_interpolation_taps,
 )

@@ -18,6 +18,8 @@ What it computes (Horacsek & Alim, arXiv 2102.08514):
 * ``VoronoiSpline`` -- the Voronoi splines V_n of Sec. 3 (the Voronoi region's indicator convolved
   with itself), as the sum of shifted box splines Sec. 3 describes, each by the box-spline oracle;
   its ``eval_sum`` / ``adjoint`` / ``phi`` mirror the functions above.
+* ``prefilter``     -- a discrete filter on the lattice (Sec. 5.2's quasi-interpolation prefilter
+  for the D4 spline: ``d4_quasi_interpolation_taps``), computed on the world grid.
 """
 from __future__ import annotations
 
@@ -329,3 +331,54 @@ class VoronoiSpline:
             for w, d2 in ws:
                 d += w * adjoint(sp, 2 * D, lk2, shape, 2.0 * p + d2, g)
         return d
+
+
+# ----------------------------------------------------------------------------- lattice prefilter
+
+def prefilter(L, D: int, cosets, samples, taps, weights) -> np.ndarray:
+    """c(n) = sum_t w_t f(n + v_t) at every stored site n (the quasi-interpolation prefilter of
+    Sec. 5.2 is 7/3 at v = 0 and -1/18 at the 24 sites at distance sqrt(2)), with f the samples
+    at the stored sites and 0 elsewhere.
+
+    Computed on the world grid, without any coset arithmetic: the samples are placed at their
+    world positions D i + l_k of a dense array (zero at non-sites), the filter is the weighted
+    sum of copies of that array shifted by the taps, read back at the sites.  The taps must be
+    lattice vectors (checked by the membership test adj(L) v = 0 mod det L)."""
+    L = np.asarray(L, dtype=np.int64)
+    f = np.asarray(samples, dtype=np.float64)
+    s = L.shape[0]
+    taps = np.asarray(taps, dtype=np.int64).reshape(-1, s)
+    det = int(round(np.linalg.det(L)))
+    adj = np.round(np.linalg.inv(L) * det).astype(np.int64)
+    if np.any((taps @ adj.T) % abs(det) != 0):
+        raise ValueError("filter taps must be lattice vectors")
+    dims = f.shape[1:]
+    R = int(np.abs(taps).max()) if taps.size else 0
+    W = np.zeros(tuple(D * n + 2 * R for n in dims))
+    for k, lk in enumerate(np.asarray(cosets, dtype=np.int64).reshape(-1, s)):
+        W[tuple(slice(R + lk[a], R + lk[a] + D * dims[a], D) for a in range(s))] = f[k]
+    C = np.zeros_like(W)
+    for v, w in zip(taps, weights):
+        # C[x] += w W[x + v] wherever x + v lies in the array
+        dst = tuple(slice(max(0, -v[a]), W.shape[a] - max(0, v[a])) for a in range(s))
+        src = tuple(slice(max(0, v[a]), W.shape[a] - max(0, -v[a])) for a in range(s))
+        C[dst] += float(w) * W[src]
+    out = np.empty_like(f)
+    for k, lk in enumerate(np.asarray(cosets, dtype=np.int64).reshape(-1, s)):
+        out[k] = C[tuple(slice(R + lk[a], R + lk[a] + D * dims[a], D) for a in range(s))]
+    return out
+
+
+def d4_quasi_interpolation_taps():
+    """Sec. 5.2: 7/3 at the origin and -1/18 at the 24 D4 sites at distance sqrt(2), the vectors
+    with two entries +-1 and two zeros."""
+    taps, w = [(0, 0, 0, 0)], [7.0 / 3.0]
+    for a in range(4):
+        for b in range(a + 1, 4):
+            for sa in (1, -1):
+                for sb in (1, -1):
+                    v = [0, 0, 0, 0]
+                    v[a], v[b] = sa, sb
+                    taps.append(tuple(v))
+                    w.append(-1.0 / 18.0)
+    return np.array(taps, dtype=np.int32), np.array(w)

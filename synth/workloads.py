@@ -14,7 +14,7 @@ from dataclasses import dataclass
 import numpy as np
 
 __all__ = ["LatticeSpec", "SplineSpec", "LATTICES", "SPLINES", "Workload", "WORKLOADS",
-           "interior_box", "make_rng", "uniform_points", "coefficients", "marschner_lobb",
+           "interior_box", "make_rng", "uniform_points", "coefficients", "marschner_lobb", "gaussian", "D4_GAUSS_SIGMA",
            "site_positions", "ray_setup", "ray_points", "batch_volumes"]
 
 SEED_BASE = 2102
@@ -47,6 +47,10 @@ LATTICES = {
     # D4* in the integer frame: all coordinates of equal parity (Sec. 5.2 mentions D4*)
     "d4s": LatticeSpec("d4s", ((2, 0, 0, 1), (0, 2, 0, 1), (0, 0, 2, 1), (0, 0, 0, 1)), 2,
                        ((0, 0, 0, 0), (1, 1, 1, 1))),
+    # Sec. 5.2 L_D4: even coordinate sum, eight cosets of 2Z^4 (the points of {0,1}^4 of even sum)
+    "d4": LatticeSpec("d4", ((-1, 0, 0, 0), (1, 0, -1, -1), (0, -1, 0, 1), (0, -1, 1, 0)), 2,
+                      ((0, 0, 0, 0), (0, 0, 1, 1), (0, 1, 0, 1), (0, 1, 1, 0), (1, 0, 0, 1), (1, 0, 1, 0),
+                       (1, 1, 0, 0), (1, 1, 1, 1))),
 }
 
 _BCC_RD = ((-1, 1, 1, -1), (1, -1, 1, -1), (1, 1, -1, -1))
@@ -68,6 +72,11 @@ SPLINES = {
                                                (1, 1, 1, 1, -1, -1, -1, -1),
                                                (1, 1, -1, -1, 1, 1, -1, -1),
                                                (1, -1, 1, -1, 1, -1, 1, -1))),
+    # Sec. 5.2: the same 8 directions on D4 (240 lookups)
+    "d4_8dir": SplineSpec("d4_8dir", "d4", ((1, 1, 1, 1, 1, 1, 1, 1),
+                                             (1, 1, 1, 1, -1, -1, -1, -1),
+                                             (1, 1, -1, -1, 1, 1, -1, -1),
+                                             (1, -1, 1, -1, 1, -1, 1, -1))),
     # Table 1: quartic truncated rhombic dodecahedron on BCC (7 directions)
     "bcc_quartic": SplineSpec("bcc_quartic", "bcc", ((2, 0, 0, -1, 1, 1, -1), (0, 2, 0, 1, -1, 1, -1),
                                                      (0, 0, 2, 1, 1, -1, -1))),
@@ -125,6 +134,16 @@ WORKLOADS = {
     # 4-D case: 2 x 48^4, 2^24 queries
     "d4s_8dir_48": Workload("d4s_8dir_48", "d4s_8dir", (48, 48, 48, 48), "uniform", 1 << 24, SEED_BASE + 4),
 }
+
+
+# Sec. 5.2's approximation experiment: a Gaussian with mean 0 and sigma = 0.125 on [-0.5, 0.5]^4,
+# sampled on the scaled lattice h L_D4 for h = 0.5 / 2^j
+D4_GAUSS_SIGMA = 0.125
+
+
+def gaussian(p: np.ndarray, sigma: float = D4_GAUSS_SIGMA) -> np.ndarray:
+    """exp(-|p|^2 / (2 sigma^2)) (unnormalised) at points p (..., s)."""
+    return np.exp(-(np.asarray(p, dtype=np.float64) ** 2).sum(axis=-1) / (2.0 * sigma * sigma))
 
 
 def make_rng(seed: int, stream: int = 0) -> np.random.Generator:
