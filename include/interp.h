@@ -79,6 +79,21 @@ const char *interp_table_digest(void);
 interp_status interp_create(int s, const int32_t *L, const int32_t *xi, int n, const int32_t *dims,
                             interp_dtype storage, interp_t **out);
 
+/*
+ * interp_create_named -- the same for a built-in spline named by interp_spline_name(i): any
+ * built-in box spline, or a Voronoi spline, which has no direction matrix.  The Voronoi
+ * splines (Sec. 3: V_0 = chi, 1/|det L| on the Voronoi region of L; V_n = V_0 * V_{n-1}; the
+ * basis is phi = |det L| V_n) are built in on their own lattices:
+ *   "bcc_voronoi1", "bcc_voronoi2"   BCC, L = L_BCC of Sec. 3 (integer frame, 2 cosets, D = 2)
+ *   "fcc_voronoi1", "fcc_voronoi2"   FCC, L = L_FCC of Sec. 3 (4 cosets, D = 2)
+ * dims, storage and the coefficient layout are as for interp_create (coset k of the lattice's
+ * Cartesian coset decomposition, as reported by interp_info).
+ *
+ * Errors: EINVAL (null pointers, dims < 1, bad storage), EUNSUPPORTED (no built-in spline of that
+ * name, or no FP16/BF16 kernels built for it), ESIZE, ENOMEM, ECUDA.  On error *out is NULL.
+ */
+interp_status interp_create_named(const char *spline, const int32_t *dims, interp_dtype storage, interp_t **out);
+
 /* Release the handle and its device memory (NULL is a no-op). Synchronises the device. */
 void interp_destroy(interp_t *h);
 
@@ -92,6 +107,7 @@ typedef struct {
     double fma_grad_per_query;    /* FP32 FMAs of one value + gradient evaluation           */
     int64_t coeff_count;          /* n_cosets * prod(dims)                                  */
     const char *name;
+    int kind;                     /* 0: box spline; n >= 1: Voronoi spline V_n              */
 } interp_info_t;
 interp_status interp_info(const interp_t *h, interp_info_t *info);
 
@@ -104,6 +120,24 @@ interp_status interp_info(const interp_t *h, interp_info_t *info);
  */
 interp_status interp_set_coeffs(interp_t *h, const void *src, interp_dtype src_dtype, int src_on_device,
                                 void *stream);
+
+/*
+ * interp_prefilter -- set the coefficients to a discrete filter of samples on the lattice,
+ *     c(n) = sum_t w_t f(n + v_t)      for every stored site n = D i + l_k,
+ * with f the samples at the stored sites and zero outside them.  Sec. 5.2 prefilters the D4
+ * spline's samples this way (7/3 at v = 0, -1/18 at the 24 lattice vectors of length sqrt 2), so
+ * that the interpolant of a function's samples converges at the spline's full order; any filter
+ * whose taps are lattice vectors is accepted.
+ *   samples  device, FP32, n_cosets x prod(dims), coset-major, last axis fastest (the layout of
+ *            interp_set_coeffs); read only; must not alias the handle's storage.
+ *   taps     host, ntaps x s int32 lattice vectors with |v_a| <= 64; 1 <= ntaps <= 64.
+ *   weights  host, ntaps FP32.
+ * Sums are FP32 in tap order; the result is rounded once to the storage type.  Stream-ordered,
+ * allocates nothing.  Errors: EINVAL (null pointer, ntaps out of range, a tap that is not a
+ * lattice vector or too long), ECUDA.
+ */
+interp_status interp_prefilter(interp_t *h, const float *samples, int ntaps, const int32_t *taps, const float *weights,
+                               void *stream);
 
 /*
  * interp_eval -- out[q] = f(pts[q]) for q < npts (Sec. 4, Algorithm 1, per query: coset loop,

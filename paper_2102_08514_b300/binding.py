@@ -36,7 +36,7 @@ class InterpInfo(ctypes.Structure):
                 ("dims", ctypes.c_int * 4), ("cosets", (ctypes.c_int32 * 4) * 8),
                 ("lookups_per_query", ctypes.c_double), ("fma_value_per_query", ctypes.c_double),
                 ("fma_grad_per_query", ctypes.c_double), ("coeff_count", ctypes.c_int64),
-                ("name", ctypes.c_char_p)]
+                ("name", ctypes.c_char_p), ("kind", ctypes.c_int)]
 
 
 class Rays(ctypes.Structure):
@@ -66,10 +66,12 @@ def load(path: str = LIB_PATH):
     lib.interp_spline_name.restype = ctypes.c_char_p
     lib.interp_table_digest.restype = ctypes.c_char_p
     lib.interp_create.argtypes = [I, P, P, I, P, I, ctypes.POINTER(ctypes.c_void_p)]
+    lib.interp_create_named.argtypes = [ctypes.c_char_p, P, I, ctypes.POINTER(ctypes.c_void_p)]
     lib.interp_destroy.argtypes = [P]
     lib.interp_destroy.restype = None
     lib.interp_info.argtypes = [P, ctypes.POINTER(InterpInfo)]
     lib.interp_set_coeffs.argtypes = [P, P, I, I, P]
+    lib.interp_prefilter.argtypes = [P, P, I, P, P, P]
     lib.interp_eval.argtypes = [P, P, I64, P, P]
     lib.interp_eval_grad.argtypes = [P, P, I64, P, P, P]
     lib.interp_backward.argtypes = [P, P, I64, P, P, P, P]
@@ -91,7 +93,7 @@ def load(path: str = LIB_PATH):
     for f in (lib.interp_batch_create, lib.interp_batch_autotune, lib.interp_batch_tile, lib.interp_batch_set_tile,
               lib.interp_batch_run):
         f.restype = I
-    for f in (lib.interp_create, lib.interp_info, lib.interp_set_coeffs, lib.interp_eval, lib.interp_eval_grad,
+    for f in (lib.interp_create, lib.interp_create_named, lib.interp_info, lib.interp_prefilter, lib.interp_set_coeffs, lib.interp_eval, lib.interp_eval_grad,
               lib.interp_backward, lib.interp_debug_indices, lib.interp_backward_noalloc):
         f.restype = I
     _lib = lib
@@ -100,7 +102,7 @@ def load(path: str = LIB_PATH):
 
 def exported_symbols() -> list[str]:
     return ["interp_strerror", "interp_num_splines", "interp_spline_name", "interp_table_digest",
-            "interp_create", "interp_destroy", "interp_info", "interp_set_coeffs", "interp_eval",
+            "interp_create", "interp_create_named", "interp_destroy", "interp_prefilter", "interp_info", "interp_set_coeffs", "interp_eval",
             "interp_eval_grad", "interp_backward", "interp_debug_indices", "interp_backward_noalloc",
             "interp_batch_create", "interp_batch_autotune", "interp_batch_tile", "interp_batch_set_tile",
             "interp_batch_run", "interp_batch_destroy", "interp_eval_rays", "interp_eval_host",
@@ -149,6 +151,15 @@ def table_digest() -> str:
 
 # ----------------------------------------------------------------------------- C-named wrappers
 
+def interp_create_named(name: str, dims, storage: int = INTERP_F32):
+    """Create a handle for the built-in spline ``name`` (box or Voronoi spline)."""
+    dims = np.ascontiguousarray(dims, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(load().interp_create_named(name.encode(), dims.ctypes.data, storage, ctypes.byref(h)),
+           "interp_create_named")
+    return h
+
+
 def interp_create(L, xi, dims, storage: int = INTERP_F32):
     """Create a handle for lattice L (s x s) and direction matrix xi (s x n); dims = samples per
     axis of every coset array.  Returns an opaque ctypes pointer."""
@@ -182,6 +193,34 @@ def interp_set_coeffs(h, coeffs, stream=None):
     c = coeffs.contiguous()
     _check(load().interp_set_coeffs(h, ctypes.c_void_p(c.data_ptr()), dt, int(c.is_cuda),
                                     _stream(stream) if c.is_cuda else _stream(stream)), "interp_set_coeffs")
+
+
+def interp_prefilter(h, samples, taps, weights, stream=None):
+    """coeffs = sum_t w_t samples(n + v_t) (Sec. 5.2's prefilter); samples: CUDA float32 tensor in
+    the coefficient layout, taps: (ntaps, s) lattice vectors, weights: (ntaps,)."""
+    import torch
+    f = _dptr(samples, "samples", torch.float32)
+    t = np.ascontiguousarray(taps, dtype=np.int32)
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    if t.ndim != 2 or w.shape != (t.shape[0],):
+        raise ValueError("taps must be (ntaps, s) and weights (ntaps,)")
+    _check(load().interp_prefilter(h, f, t.shape[0], t.ctypes.data, w.ctypes.data, _stream(stream)),
+           "interp_prefilter")
+
+
+def d4_quasi_interpolation_filter():
+    """Sec. 5.2's prefilter for the 8-direction spline on D4: 7/3 at the origin and -1/18 at the
+    24 lattice vectors of length sqrt(2) (two entries +-1, two zeros).  Returns (taps, weights)."""
+    taps = [(0, 0, 0, 0)]
+    for a in range(4):
+        for b in range(a + 1, 4):
+            for sa in (1, -1):
+                for sb in (1, -1):
+                    v = [0, 0, 0, 0]
+                    v[a], v[b] = sa, sb
+                    taps.append(tuple(v))
+    w = [7.0 / 3.0] + [-1.0 / 18.0] * 24
+    return np.asarray(taps, dtype=np.int32), np.asarray(w, dtype=np.float32)
 
 
 def interp_eval(h, pts, out, stream=None):
@@ -297,8 +336,8 @@ def interp_batch_destroy(b):
 
 
 class Batch:
-    """Many (Interpolator, points, output) triples evaluated by one persistent launch per
-    dimension, replayed from a CUDA graph."""
+    """Many (Interpolator, points, output) triples evaluated by one persistent launch (plus one
+    launch per handle outside the persistent kernel's splines), replayed from a CUDA graph."""
 
     def __init__(self, items):
         self._keep = list(items)        # keep the handles and tensors alive
@@ -309,9 +348,15 @@ class Batch:
         return self.tiles()
 
     def tiles(self) -> dict:
-        """Tile size per 3-D spline (4-D handles run their own launch and have none)."""
-        names = sorted({it.info.name.decode() for it, _, _ in self._keep if it.s == 3})
-        return {n: interp_batch_tile(self._b, n) for n in names}
+        """Tile size per spline of the persistent kernel (handles that run their own launch, the
+        4-D ones and the 3-D splines outside the persistent kernel, have none)."""
+        out = {}
+        for n in sorted({it.info.name.decode() for it, _, _ in self._keep if it.s == 3}):
+            try:
+                out[n] = interp_batch_tile(self._b, n)
+            except InterpError:
+                pass
+        return out
 
     def set_tiles(self, tiles: dict):
         for n, t in tiles.items():
@@ -338,20 +383,32 @@ STORAGE = {"f32": INTERP_F32, "f16": INTERP_F16, "bf16": INTERP_BF16}
 
 
 class Interpolator:
-    """A handle plus its shape: f(x) = sum_k sum_i c_k[i] phi(x - D i - l_k) on one device."""
+    """A handle plus its shape: f(x) = sum_k sum_i c_k[i] phi(x - D i - l_k) on one device.
 
-    def __init__(self, L, xi, dims, storage: str = "f32", coeffs=None):
-        self.L = np.asarray(L, dtype=np.int32)
-        self.xi = np.asarray(xi, dtype=np.int32)
+    Interpolator(L, xi, dims) selects a box spline by lattice and direction matrix;
+    Interpolator.named(name, dims) any built-in spline by name (the Voronoi splines have no
+    direction matrix)."""
+
+    def __init__(self, L, xi, dims, storage: str = "f32", coeffs=None, *, name: str | None = None):
         self.dims = tuple(int(d) for d in dims)
         self.storage = storage
-        self._h = interp_create(self.L, self.xi, self.dims, STORAGE[storage])
+        if name is not None:
+            self._h = interp_create_named(name, self.dims, STORAGE[storage])
+            self.L = self.xi = None
+        else:
+            self.L = np.asarray(L, dtype=np.int32)
+            self.xi = np.asarray(xi, dtype=np.int32)
+            self._h = interp_create(self.L, self.xi, self.dims, STORAGE[storage])
         self.info = interp_info(self._h)
         self.s = self.info.s
         self.n_cosets = self.info.n_cosets
         self.shape = (self.n_cosets,) + self.dims
         if coeffs is not None:
             self.set_coeffs(coeffs)
+
+    @classmethod
+    def named(cls, name: str, dims, storage: str = "f32", coeffs=None):
+        return cls(None, None, dims, storage, coeffs, name=name)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -372,6 +429,12 @@ class Interpolator:
         if tuple(coeffs.shape) != self.shape:
             raise ValueError(f"coefficients must have shape {self.shape}, got {tuple(coeffs.shape)}")
         interp_set_coeffs(self._h, coeffs, stream)
+
+    def prefilter(self, samples, taps, weights, stream=None):
+        """Coefficients from samples by a lattice filter (interp_prefilter)."""
+        if tuple(samples.shape) != self.shape:
+            raise ValueError(f"samples must have shape {self.shape}, got {tuple(samples.shape)}")
+        interp_prefilter(self._h, samples, taps, weights, stream)
 
     def eval(self, pts, out=None, stream=None):
         import torch

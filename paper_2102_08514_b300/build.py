@@ -86,13 +86,11 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False, job
             jobsl.append(([nvcc(), *NVCC_FLAGS, *extra, *inc, f"-DINTERP_SPLINE={name}", f"-DINTERP_PART={part}",
                            "-c", os.path.join(CSRC, "ops_inst.cu"), "-o", o], None))
             objs.append(o)
-    for dim in (3, 4):
-        o = os.path.join(objdir, f"batch_{dim}d.o")
-        jobsl.append(([nvcc(), *NVCC_FLAGS, *extra, *inc, f"-DINTERP_BATCH_DIM={dim}", "-c",
-                       os.path.join(CSRC, "batch_inst.cu"), "-o", o], None))
-        objs.append(o)
-    # the 4-D spline's units need several GB each: at most two of them run at a time
-    big = [j for j in jobsl if "d4s" in " ".join(j[0]) or "BATCH_DIM=4" in " ".join(j[0])]
+    o = os.path.join(objdir, "batch_3d.o")
+    jobsl.append(([nvcc(), *NVCC_FLAGS, *extra, *inc, "-c", os.path.join(CSRC, "batch_inst.cu"), "-o", o], None))
+    objs.append(o)
+    # the units of the large splines need several GB each: at most two of them run at a time
+    big = [j for j in jobsl if any(k in " ".join(j[0]) for k in ("d4s", "voronoi2", "voronoi3"))]
     small = [j for j in jobsl if j not in big]
     logs = []
     with cf.ThreadPoolExecutor(max_workers=2) as exb, \

@@ -1,21 +1,11 @@
-// batch_inst.cu -- the persistent batched kernel over the 3-D splines (-DINTERP_BATCH_DIM=3) and
-// the spline-name lookup of each dimension (-DINTERP_BATCH_DIM=3 or 4).
+// batch_inst.cu -- the persistent batched kernel over the 3-D splines listed in
+// INTERP_GEN_BATCH_3D, and the lookup of a spline name in that list.
 #include "kernels.cuh"
 #include "registry.h"
 
-#ifndef INTERP_BATCH_DIM
-#error "compile with -DINTERP_BATCH_DIM=3 or 4"
-#endif
-
-#if INTERP_BATCH_DIM == 3
-#define IB_LIST INTERP_GEN_SPLINES_3D
-#define IB_NAMES INTERP_GEN_NAMES_3D
+#define IB_LIST INTERP_GEN_BATCH_3D
+#define IB_NAMES INTERP_GEN_BATCH_NAMES_3D
 #define IB_FN(x) x##_3d
-#else
-#define IB_LIST INTERP_GEN_SPLINES_4D
-#define IB_NAMES INTERP_GEN_NAMES_4D
-#define IB_FN(x) x##_4d
-#endif
 
 namespace ibr {
 
@@ -31,7 +21,6 @@ int IB_FN(batch_kind)(const char *name)
     return -1;
 }
 
-#if INTERP_BATCH_DIM == 3
 // CTAs of the persistent kernel that fit on the device at once (grid size of one wave)
 cudaError_t IB_FN(batch_grid)(int *grid)
 {
@@ -49,6 +38,5 @@ cudaError_t IB_FN(batch_launch)(const ibl::BatchVol *vols, int nvol, int64_t tot
     ib::k_batch<IB_LIST><<<grid, 128, 0, st>>>(vols, nvol, total_tiles, counter);
     return cudaPeekAtLastError();
 }
-#endif  // the 4-D handles of a batch run the (piece-binned) evaluation kernel instead
 
 }  // namespace ibr

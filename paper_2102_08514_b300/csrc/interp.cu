@@ -86,6 +86,48 @@ __global__ void k_pad_copy(const ST *__restrict__ src, CT *__restrict__ dst, int
         dst[padded_offset(L, e)] = convert_to<ST, CT>(src[e]);
 }
 
+// the taps of a lattice filter resolved per output coset: tap t of output coset k reads the
+// samples of coset src[k][t] at index i + shift[k][t] (passed by value as a kernel parameter)
+constexpr int kMaxTaps = 64;
+struct PrefilterTaps {
+    int ntaps;
+    float w[kMaxTaps];
+    signed char src[8][kMaxTaps];
+    signed char shift[8][kMaxTaps][4];
+};
+
+// c_k[i] = sum_t w_t f_src[i + shift] over the taps (samples taken as zero outside the arrays),
+// rounded to the storage type and written to the interior of the padded, bricked arrays.  One
+// thread per output site in sample order (row-major), so the reads of every tap are coalesced.
+template <class CT>
+__global__ void k_prefilter(const float *__restrict__ f, CT *__restrict__ dst, int64_t total, ibl::Layout L,
+                            PrefilterTaps tp)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        int idx[4] = {0, 0, 0, 0};
+        int64_t r = e;
+        for (int a = L.s - 1; a >= 0; --a) {
+            idx[a] = (int)(r % L.n[a]);
+            r /= L.n[a];
+        }
+        const int k = (int)r;
+        float acc = 0.0f;
+        for (int t = 0; t < tp.ntaps; ++t) {
+            int64_t off = tp.src[k][t];
+            bool in = true;
+            for (int a = 0; a < L.s; ++a) {
+                const int j = idx[a] + tp.shift[k][t][a];
+                in &= (unsigned)j < (unsigned)L.n[a];
+                off = off * L.n[a] + j;
+            }
+            if (in) acc = fmaf(tp.w[t], __ldg(f + off), acc);
+        }
+        int p[4];
+        for (int a = 0; a < 4; ++a) p[a] = idx[a] + L.pad;
+        dst[ibl::elem_offset(L, k, p)] = convert_to<float, CT>(acc);
+    }
+}
+
 // dst (unpadded FP32) += interior of the padded FP32 gradient buffer
 __global__ void k_unpad_add(const float *__restrict__ pad_buf, float *__restrict__ dst, int64_t total, ibl::Layout L)
 {
@@ -265,6 +307,51 @@ static cudaError_t eval_launch(const interp *h, const float *pts, int64_t npts, 
     return (binned ? h->ops->eval_binned : h->ops->eval)[dt][mode](pts, npts, h->coeffs, h->lay, out, grad, gout, st);
 }
 
+// the handle for a registry entry: validate dims and storage, lay out and zero the padded arrays
+static interp_status create_handle(const SplineOps *ops, const int32_t *dims, interp_dtype storage, interp_t **out)
+{
+    const int s = ops->s;
+    if (storage != INTERP_F32 && storage != INTERP_F16 && storage != INTERP_BF16) return INTERP_EINVAL;
+    for (int a = 0; a < s; ++a)
+        if (dims[a] < 1) return INTERP_EINVAL;
+    if (storage != INTERP_F32 && !ops->eval[storage == INTERP_F16 ? 1 : 2][0]) return INTERP_EUNSUPPORTED;
+
+    interp *h = new (std::nothrow) interp;
+    if (!h) return INTERP_ENOMEM;
+    h->ops = ops;
+    h->s = s;
+    h->storage = storage;
+    const int pad = 2 * ops->halo;
+    int64_t cc = 1;
+    for (int a = 0; a < s; ++a) {
+        h->dims[a] = dims[a];
+        cc *= dims[a];
+    }
+    const int esz = storage == INTERP_F32 ? 4 : 2;
+    // cosets side by side in the bricks or in separate arrays: separate by default (measured
+    // faster on the BCC quintic workload); INTERP_B300_INTERLEAVE=1 selects the other layout
+    const char *il = std::getenv("INTERP_B300_INTERLEAVE");
+    const bool inter = il && il[0] == '1';
+    if (!ibl::make_layout(h->lay, s, h->dims, pad, esz, ops->M, inter) ||
+        !ibl::make_layout(h->lay32, s, h->dims, pad, 4, ops->M, inter)) {
+        delete h;
+        return INTERP_ESIZE;
+    }
+    h->coeff_count = cc * ops->M;
+    cudaGetDevice(&h->device);
+    const size_t bytes = (size_t)h->lay.total * esz;
+    cudaError_t e = cudaMalloc(&h->coeffs, bytes);
+    if (e == cudaSuccess) e = cudaMemset(h->coeffs, 0, bytes);
+    if (e != cudaSuccess) {
+        cudaFree(h->coeffs);
+        delete h;
+        cudaGetLastError();
+        return cuda_status(e);
+    }
+    *out = h;
+    return INTERP_OK;
+}
+
 extern "C" {
 
 const char *interp_strerror(interp_status st)
@@ -305,7 +392,8 @@ interp_status interp_create(int s, const int32_t *L, const int32_t *xi, int n, c
     const auto want = canonical_columns(s, xi, n);
     const SplineOps *ops = nullptr;
     for (const auto &o : registry()) {
-        if (o.s != s || o.nxi != n || o.D != li.D || o.M != (int)li.cosets.size()) continue;
+        // box splines only: a Voronoi spline's recorded generators are not a direction matrix
+        if (o.kind != 0 || o.s != s || o.nxi != n || o.D != li.D || o.M != (int)li.cosets.size()) continue;
         if (canonical_columns(s, o.xi, o.nxi) != want) continue;
         bool same = true;
         for (int k = 0; k < o.M && same; ++k)
@@ -316,42 +404,17 @@ interp_status interp_create(int s, const int32_t *L, const int32_t *xi, int n, c
         }
     }
     if (!ops) return INTERP_EUNSUPPORTED;
-    if (storage != INTERP_F32 && !ops->eval[storage == INTERP_F16 ? 1 : 2][0]) return INTERP_EUNSUPPORTED;
+    return create_handle(ops, dims, storage, out);
+}
 
-    interp *h = new (std::nothrow) interp;
-    if (!h) return INTERP_ENOMEM;
-    h->ops = ops;
-    h->s = s;
-    h->storage = storage;
-    const int pad = 2 * ops->halo;
-    int64_t cc = 1;
-    for (int a = 0; a < s; ++a) {
-        h->dims[a] = dims[a];
-        cc *= dims[a];
-    }
-    const int esz = storage == INTERP_F32 ? 4 : 2;
-    // cosets side by side in the bricks or in separate arrays: separate by default (measured
-    // faster on the BCC quintic workload); INTERP_B300_INTERLEAVE=1 selects the other layout
-    const char *il = std::getenv("INTERP_B300_INTERLEAVE");
-    const bool inter = il && il[0] == '1';
-    if (!ibl::make_layout(h->lay, s, h->dims, pad, esz, ops->M, inter) ||
-        !ibl::make_layout(h->lay32, s, h->dims, pad, 4, ops->M, inter)) {
-        delete h;
-        return INTERP_ESIZE;
-    }
-    h->coeff_count = cc * ops->M;
-    cudaGetDevice(&h->device);
-    const size_t bytes = (size_t)h->lay.total * esz;
-    cudaError_t e = cudaMalloc(&h->coeffs, bytes);
-    if (e == cudaSuccess) e = cudaMemset(h->coeffs, 0, bytes);
-    if (e != cudaSuccess) {
-        cudaFree(h->coeffs);
-        delete h;
-        cudaGetLastError();
-        return cuda_status(e);
-    }
-    *out = h;
-    return INTERP_OK;
+interp_status interp_create_named(const char *spline, const int32_t *dims, interp_dtype storage, interp_t **out)
+{
+    if (!out) return INTERP_EINVAL;
+    *out = nullptr;
+    if (!spline || !dims) return INTERP_EINVAL;
+    for (const auto &o : registry())
+        if (std::strcmp(o.name, spline) == 0) return create_handle(&o, dims, storage, out);
+    return INTERP_EUNSUPPORTED;
 }
 
 void interp_destroy(interp_t *h)
@@ -390,7 +453,55 @@ interp_status interp_info(const interp_t *h, interp_info_t *info)
     info->fma_grad_per_query = o.fma_grad;
     info->coeff_count = h->coeff_count;
     info->name = o.name;
+    info->kind = o.kind;
     return INTERP_OK;
+}
+
+interp_status interp_prefilter(interp_t *h, const float *samples, int ntaps, const int32_t *taps, const float *weights,
+                               void *stream)
+{
+    if (!h || !samples || !taps || !weights || ntaps < 1 || ntaps > kMaxTaps) return INTERP_EINVAL;
+    const SplineOps &o = *h->ops;
+    const int s = o.s, M = o.M, D = o.D;
+    PrefilterTaps tp{};
+    tp.ntaps = ntaps;
+    for (int t = 0; t < ntaps; ++t) {
+        tp.w[t] = weights[t];
+        for (int a = 0; a < s; ++a)
+            if (taps[t * s + a] < -64 || taps[t * s + a] > 64) return INTERP_EINVAL;
+        // l_k + v lies on coset k' at index shift (l_k + v - l_k') / D; no coset: v is not a
+        // lattice vector
+        for (int k = 0; k < M; ++k) {
+            int kk = -1;
+            for (int c = 0; c < M && kk < 0; ++c) {
+                bool same = true;
+                for (int a = 0; a < s; ++a) {
+                    const int u = o.cosets[k * s + a] + taps[t * s + a] - o.cosets[c * s + a];
+                    same &= ((u % D) + D) % D == 0;
+                }
+                if (same) kk = c;
+            }
+            if (kk < 0) return INTERP_EINVAL;
+            tp.src[k][t] = (signed char)kk;
+            for (int a = 0; a < s; ++a)
+                tp.shift[k][t][a] = (signed char)((o.cosets[k * s + a] + taps[t * s + a] - o.cosets[kk * s + a]) / D);
+        }
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const unsigned grid = (unsigned)std::min<int64_t>((h->coeff_count + 255) / 256, 148 * 32);
+    switch (h->storage) {
+    case INTERP_F32:
+        k_prefilter<float><<<grid, 256, 0, st>>>(samples, static_cast<float *>(h->coeffs), h->coeff_count, h->lay, tp);
+        break;
+    case INTERP_F16:
+        k_prefilter<__half><<<grid, 256, 0, st>>>(samples, static_cast<__half *>(h->coeffs), h->coeff_count, h->lay, tp);
+        break;
+    default:
+        k_prefilter<__nv_bfloat16><<<grid, 256, 0, st>>>(samples, static_cast<__nv_bfloat16 *>(h->coeffs),
+                                                         h->coeff_count, h->lay, tp);
+        break;
+    }
+    return cuda_status(cudaPeekAtLastError());
 }
 
 interp_status interp_set_coeffs(interp_t *h, const void *src, interp_dtype src_dtype, int src_on_device, void *stream)
@@ -666,11 +777,11 @@ struct interp_batch {
         int64_t total = 0;
         int grid = 0;
     };
-    Group g[2];                                   // [0]: 3-D handles, [1]: 4-D handles
+    Group g[2];                                   // [0]: persistent-kernel handles, [1]: the others
     unsigned long long *d_counters = nullptr;     // one work counter per group
     std::vector<std::string> names[2];            // spline name of every volume, per group
     std::map<std::string, int> tiles;             // queries per tile, per spline
-    std::vector<const interp *> vols4;             // the 4-D handles (evaluated by their own launch)
+    std::vector<const interp *> own;              // handles evaluated by their own launch (group 1)
     cudaStream_t cs = nullptr;                    // private stream for graph capture
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -704,9 +815,9 @@ cudaError_t batch_upload(interp_batch *b)
     return cudaSuccess;
 }
 
-// enqueue one batched evaluation: the 3-D handles in one persistent launch (counter reset +
-// kernel); the 4-D handles, whose 6-piece spline needs the piece-binned kernel, as one
-// evaluation launch each
+// enqueue one batched evaluation: the handles of the persistent kernel's splines in one launch
+// (counter reset + kernel); the others (4-D, and 3-D splines whose pieces or registers would
+// slow the persistent kernel for everyone) as one evaluation launch each
 cudaError_t batch_enqueue(interp_batch *b, cudaStream_t st)
 {
     auto &G = b->g[0];
@@ -716,10 +827,10 @@ cudaError_t batch_enqueue(interp_batch *b, cudaStream_t st)
             e = ibr::batch_launch_3d(G.d_vols, (int)G.vols.size(), G.total, b->d_counters, G.grid, st);
         if (e != cudaSuccess) return e;
     }
-    for (size_t v = 0; v < b->vols4.size(); ++v) {
+    for (size_t v = 0; v < b->own.size(); ++v) {
         const ibl::BatchVol &bv = b->g[1].vols[v];
         if (bv.npts == 0) continue;
-        cudaError_t e = eval_launch(b->vols4[v], bv.pts, bv.npts, bv.out, nullptr, nullptr, 0, st);
+        cudaError_t e = eval_launch(b->own[v], bv.pts, bv.npts, bv.out, nullptr, nullptr, 0, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -766,24 +877,20 @@ interp_status interp_batch_create(const interp_batch_item *items, int n, interp_
             delete b;
             return INTERP_EUNSUPPORTED;
         }
-        const int gi = it.vol->s == 3 ? 0 : 1;
-        const int kind = gi == 0 ? ibr::batch_kind_3d(it.vol->ops->name) : ibr::batch_kind_4d(it.vol->ops->name);
-        if (kind < 0) {
-            delete b;
-            return INTERP_EUNSUPPORTED;
-        }
+        const int kind = it.vol->s == 3 ? ibr::batch_kind_3d(it.vol->ops->name) : -1;
+        const int gi = kind >= 0 ? 0 : 1;
         ibl::BatchVol bv{};
         bv.c = static_cast<const float *>(it.vol->coeffs);
         bv.pts = it.pts;
         bv.out = it.out;
         bv.npts = it.npts;
-        bv.kind = kind;
+        bv.kind = kind >= 0 ? kind : 0;
         bv.tile = kDefaultTile;
         bv.L = it.vol->lay;
         b->g[gi].vols.push_back(bv);
         b->names[gi].push_back(it.vol->ops->name);
         if (gi == 0) b->tiles.emplace(it.vol->ops->name, kDefaultTile);
-        else b->vols4.push_back(it.vol);
+        else b->own.push_back(it.vol);
     }
     cudaError_t e = cudaMalloc(&b->d_counters, 2 * sizeof(unsigned long long));
     for (int gi = 0; gi < 2 && e == cudaSuccess; ++gi) {

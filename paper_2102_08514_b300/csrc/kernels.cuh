@@ -8,8 +8,9 @@
 //   2. symmetry fold (Sec. 4.2's reflection, taken to the full signed-permutation group): y' = |y|
 //      sorted descending by a sorting network; the signed permutation S is carried as per-slot
 //      signed strides, which is the renaming map pi of Sec. 4.3 applied to gather addresses;
-//   3. branch-free sub-region index: q = sum_i [p_i . y' - d_i >= 0] 2^i, j = sigma[q mod r]
-//      (Sec. 4.2; sigma is packed into one 64-bit constant);
+//   3. branch-free sub-region index: q = sum_i [p_i . y' - d_i >= 0] 2^i, j = sigma[q] (Sec. 4.2;
+//      the table is uncompressed, 2^Q entries: up to 64 packed into 64-bit constants, 16 four-bit
+//      entries each, larger ones a byte table in device memory);
 //   4. gather the piece's stencil c_m = c_k[i + S^-1 g_m] (Sec. 4.1, C_0(S_j));
 //   5. b = A_j c (per-monomial coefficients; A_j's nonzeros are compile-time FMA immediates), then
 //      nested Horner in t = y' - anchor_j (the greedy Horner of Sec. 4.1), optionally carrying all
@@ -178,13 +179,22 @@ __device__ __forceinline__ void reduce_axis_rt(float x, int l, int &i, float &y)
     y = (float)(v - D * i) + fr;
 }
 
-// coset shifts packed 4 bits per coordinate, so a run-time coset index can read them
+// coset shifts packed into one 64-bit word (coset_bits per entry, entries lie in [0, D)), so a
+// run-time coset index can read them
+template <class SP>
+constexpr int coset_bits()
+{
+    int b = 1;
+    while ((1 << b) < SP::D) ++b;
+    return b;
+}
+
 template <class SP>
 constexpr uint64_t cosets_packed()
 {
     uint64_t v = 0;
     for (int k = 0; k < SP::M; ++k)
-        for (int a = 0; a < SP::S; ++a) v |= (uint64_t)SP::COSET[k][a] << (4 * (k * SP::S + a));
+        for (int a = 0; a < SP::S; ++a) v |= (uint64_t)SP::COSET[k][a] << (coset_bits<SP>() * (k * SP::S + a));
     return v;
 }
 
@@ -222,11 +232,13 @@ __device__ __forceinline__ void sort_desc(Slot (&sl)[S])
     }
 }
 
-template <class SP>
-constexpr uint64_t sigma_packed()
+// word W of sigma packed 16 four-bit entries to a 64-bit word (R <= 64, K <= 15)
+template <class SP, int W>
+constexpr uint64_t sigma_word()
 {
     uint64_t v = 0;
-    for (int r = 0; r < SP::R; ++r) v |= (uint64_t)(SP::SIGMA[r] < 0 ? 15 : SP::SIGMA[r]) << (4 * r);
+    for (int r = 16 * W; r < SP::R && r < 16 * (W + 1); ++r)
+        v |= (uint64_t)(SP::SIGMA[r] < 0 ? 15 : SP::SIGMA[r]) << (4 * (r - 16 * W));
     return v;
 }
 
@@ -269,8 +281,10 @@ __device__ __forceinline__ Fold<SP::S> fold_coset(const float (&x)[SP::S], const
         if constexpr (K >= 0) {
             reduce_axis<SP::D, SP::COSET[K][a]>(x[a], idx, y);
         } else {
+            constexpr int B = coset_bits<SP>();
+            static_assert(SP::M * S * B <= 64, "the coset shifts must pack into 64 bits");
             constexpr uint64_t packed = cosets_packed<SP>();
-            const int l = (int)((packed >> (4 * (kr * S + a))) & 15u);
+            const int l = (int)((packed >> (B * (kr * S + a))) & ((1u << B) - 1u));
             reduce_axis_rt<SP::D>(x[a], l, idx, y);
         }
         ok &= (unsigned)(idx + H) < (unsigned)(v.L.n[a] + 2 * H);
@@ -300,8 +314,19 @@ __device__ __forceinline__ Fold<SP::S> fold_coset(const float (&x)[SP::S], const
             });
             q |= (acc >= 0.0f ? 1u : 0u) << i;
         });
-        constexpr uint64_t packed = sigma_packed<SP>();
-        j = (int)((packed >> (4 * (q % (unsigned)SP::R))) & 15u);
+        if constexpr (SP::R > 64) {
+            j = (int)SP::sigma_at(q);                   // byte table in device memory
+        } else {
+            static_assert(SP::K <= 15, "sigma packing holds four-bit piece indices");
+            uint64_t w = sigma_word<SP, 0>();
+            if constexpr (SP::R > 16) {
+                sfor<(SP::R + 15) / 16 - 1>([&](auto W) {
+                    constexpr int ww = decltype(W)::value + 1;
+                    if ((q >> 4) == (unsigned)ww) w = sigma_word<SP, ww>();
+                });
+            }
+            j = (int)((w >> (4 * (q & 15u))) & 15u);
+        }
     }
     f.piece = j;
     f.base = base;
@@ -635,18 +660,12 @@ namespace ib {
 // block of pixels, so its samples are close together and share coefficient sectors in L1.
 using ibl::RayGeom;
 
-template <class SP, bool GRAD>
-__global__ void __launch_bounds__(128) k_rays(RayGeom rg, DevVol<float> v, float *__restrict__ out,
-                                              float *__restrict__ pts_out)
+// ray of pixel (px, py): origin o, and the entry parameter tmin and step dt of its samples
+// inside the box [lo, hi] (sample i at o + (tmin + (i + 1/2) dt) dir); false if it misses the box
+__device__ __forceinline__ bool ray_setup(const RayGeom &rg, int px, int py, float (&o)[3], float &tmin, float &dt)
 {
-    static_assert(SP::S == 3, "rays are 3-D");
-    // 128 threads = 4 warps; a block covers 16 x 8 pixels, a warp 8 x 4
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int px = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
-    const int py = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
-    if (px >= rg.width || py >= rg.height) return;
-    float o[3];
-    float tmin = -3.0e38f, tmax = 3.0e38f;
+    float tmax = 3.0e38f;
+    tmin = -3.0e38f;
     sfor<3>([&](auto A) {
         o[A] = rg.origin[A] + ((float)px + 0.5f) * rg.du[A] + ((float)py + 0.5f) * rg.dv[A];
         if (rg.dir[A] != 0.0f) {
@@ -658,10 +677,24 @@ __global__ void __launch_bounds__(128) k_rays(RayGeom rg, DevVol<float> v, float
             tmax = -3.0e38f;                                  // parallel to the slab and outside
         }
     });
+    dt = (tmax - tmin) / (float)rg.steps;
+    return tmax > tmin;
+}
+
+template <class SP, bool GRAD>
+__global__ void __launch_bounds__(128) k_rays(RayGeom rg, DevVol<float> v, float *__restrict__ out,
+                                              float *__restrict__ pts_out)
+{
+    static_assert(SP::S == 3, "rays are 3-D");
+    // 128 threads = 4 warps; a block covers 16 x 8 pixels, a warp 8 x 4
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int px = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
+    const int py = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
+    if (px >= rg.width || py >= rg.height) return;
+    float o[3], tmin, dt;
     float val = 0.0f, g[3] = {0.0f, 0.0f, 0.0f};
     const int64_t pix = (int64_t)py * rg.width + px;
-    if (tmax > tmin) {
-        const float dt = (tmax - tmin) / (float)rg.steps;
+    if (ray_setup(rg, px, py, o, tmin, dt)) {
         for (int i = 0; i < rg.steps; ++i) {
             const float t = tmin + ((float)i + 0.5f) * dt;
             float x[3];
@@ -736,44 +769,38 @@ constexpr size_t binned_smem_bytes()
 }
 
 // classify the tile's (query, coset) items and counting-sort them by piece in shared memory:
-// on return perm[0 .. start[K]) lists the live items in piece order (ends with a barrier)
-template <class SP, class CT, int T>
-__device__ __forceinline__ void bin_tile(const float *__restrict__ pts, int64_t n, const DevVol<CT> &v, int64_t q0,
-                                         BinRec<SP::S> *rec, unsigned short *perm, unsigned short *rank,
-                                         signed char *rpiece, int *cnt, int *start)
+// on return perm[0 .. start[K]) lists the live items in piece order (ends with a barrier).
+// src(ql, x) fills the coordinates of local query ql and returns false for a query that is
+// absent or not finite (its items are dropped).
+template <class SP, class CT, int T, class Src>
+__device__ __forceinline__ void bin_tile_src(Src &&src, const DevVol<CT> &v, BinRec<SP::S> *rec,
+                                             unsigned short *perm, unsigned short *rank, signed char *rpiece,
+                                             int *cnt, int *start)
 {
     constexpr int S = SP::S, M = SP::M, K = SP::K, NI = T * M;
     const int tid = threadIdx.x;
     if (tid < K) cnt[tid] = 0;
     __syncthreads();
-    // classify: item i = (query q0 + i % T, coset i / T)
+    // classify: item i = (query i % T, coset i / T)
     for (int i = tid; i < NI; i += blockDim.x) {
         const int ql = i % T, k = i / T;
-        const int64_t q = q0 + ql;
         int j = -1;
-        if (q < n) {
-            float x[S];
-            bool finite = true;
-            sfor<S>([&](auto A) {
-                x[A] = pts[q * S + A];
-                finite &= isfinite(x[A]);
-            });
-            if (finite) {
-                const Fold<S> f = fold_coset<SP, -1, CT>(x, v, k);
-                if (f.in_range) {
-                    j = f.piece;
-                    BinRec<S> r;
-                    r.base = f.base;
-                    unsigned slots = 0;
-                    sfor<S>([&](auto A) {
-                        r.t[A] = f.t[A];
-                        slots |= ((f.sl[A].sg < 0 ? 1u : 0u) | ((unsigned)f.sl[A].ax << 1) | ((unsigned)f.sl[A].p << 3))
-                                 << (5 * A);
-                    });
-                    r.slots = slots;
-                    rec[i] = r;
-                    rank[i] = (unsigned short)atomicAdd(&cnt[j], 1);
-                }
+        float x[S];
+        if (src(ql, x)) {
+            const Fold<S> f = fold_coset<SP, -1, CT>(x, v, k);
+            if (f.in_range) {
+                j = f.piece;
+                BinRec<S> r;
+                r.base = f.base;
+                unsigned slots = 0;
+                sfor<S>([&](auto A) {
+                    r.t[A] = f.t[A];
+                    slots |= ((f.sl[A].sg < 0 ? 1u : 0u) | ((unsigned)f.sl[A].ax << 1) | ((unsigned)f.sl[A].p << 3))
+                             << (5 * A);
+                });
+                r.slots = slots;
+                rec[i] = r;
+                rank[i] = (unsigned short)atomicAdd(&cnt[j], 1);
             }
         }
         rpiece[i] = (signed char)j;
@@ -791,6 +818,27 @@ __device__ __forceinline__ void bin_tile(const float *__restrict__ pts, int64_t 
     for (int i = tid; i < NI; i += blockDim.x)
         if (rpiece[i] >= 0) perm[start[rpiece[i]] + rank[i]] = (unsigned short)i;
     __syncthreads();
+}
+
+// the same for the tile of T queries starting at q0 of the point array pts (n points)
+template <class SP, class CT, int T>
+__device__ __forceinline__ void bin_tile(const float *__restrict__ pts, int64_t n, const DevVol<CT> &v, int64_t q0,
+                                         BinRec<SP::S> *rec, unsigned short *perm, unsigned short *rank,
+                                         signed char *rpiece, int *cnt, int *start)
+{
+    constexpr int S = SP::S;
+    bin_tile_src<SP, CT, T>(
+        [&](int ql, float (&x)[S]) {
+            const int64_t q = q0 + ql;
+            if (q >= n) return false;
+            bool finite = true;
+            sfor<S>([&](auto A) {
+                x[A] = pts[q * S + A];
+                finite &= isfinite(x[A]);
+            });
+            return finite;
+        },
+        v, rec, perm, rank, rpiece, cnt, start);
 }
 
 // T queries per tile, NT threads per CTA.  With NT = 512 and a large tile the CTA fills an SM,
@@ -887,6 +935,84 @@ __global__ void __launch_bounds__(NT) k_adjoint_binned(const float *__restrict__
         sfor<K>([&](auto Jc) {
             if (j == decltype(Jc)::value) adjoint_piece<SP, decltype(Jc)::value>(f, dpad, w);
         });
+    }
+}
+
+// rays of a multi-piece spline, piece-binned: a tile holds RT = T / steps whole rays (the host
+// launches it only for steps <= T); the samples come from the ray geometry, are classified and
+// sorted by piece as in k_eval_binned, evaluated in piece order, and summed per ray in step order
+// and coset order -- the order of k_rays, so both kernels return the same sums.  One CTA per tile.
+template <class SP, bool GRAD, int T, int NT>
+__global__ void __launch_bounds__(NT) k_rays_binned(RayGeom rg, DevVol<float> v, float *__restrict__ out,
+                                                    float *__restrict__ pts_out)
+{
+    static_assert(SP::S == 3, "rays are 3-D");
+    constexpr int S = 3, M = SP::M, K = SP::K, NI = T * M;
+    constexpr int NV = GRAD ? S + 1 : 1;
+    static_assert(NI <= 65535, "item index must fit 16 bits");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    BinRec<S> *rec = reinterpret_cast<BinRec<S> *>(smem_raw);
+    float *acc = reinterpret_cast<float *>(rec + NI);
+    unsigned short *perm = reinterpret_cast<unsigned short *>(acc + NI * NV);
+    unsigned short *rank = perm + NI;
+    signed char *rpiece = reinterpret_cast<signed char *>(rank + NI);
+    __shared__ int cnt[K], start[K + 1];
+    const int tid = threadIdx.x;
+    const int steps = rg.steps;
+    const int RT = T / steps;
+    const int64_t npix = (int64_t)rg.width * rg.height;
+    const int64_t r0 = (int64_t)blockIdx.x * RT;
+    for (int i = tid; i < NI * NV; i += blockDim.x) acc[i] = 0.0f;
+    // sample ql of the tile: ray r0 + ql / steps, step ql % steps
+    auto sample = [&](int ql, float (&x)[S]) {
+        const int rl = ql / steps, i = ql - rl * steps;
+        const int64_t pix = r0 + rl;
+        if (rl >= RT || pix >= npix) return false;
+        float o[3], tmin, dt;
+        if (!ray_setup(rg, (int)(pix % rg.width), (int)(pix / rg.width), o, tmin, dt)) return false;
+        const float t = tmin + ((float)i + 0.5f) * dt;
+        sfor<S>([&](auto A) { x[A] = fmaf(t, rg.dir[A], o[A]); });
+        return true;
+    };
+    if (pts_out) {
+        for (int ql = tid; ql < RT * steps; ql += blockDim.x) {
+            const int64_t q = r0 * steps + ql;
+            if (q >= npix * steps) break;
+            float x[S];
+            if (!sample(ql, x)) sfor<S>([&](auto A) { x[A] = __int_as_float(0x7fc00000); });
+            sfor<S>([&](auto A) { pts_out[q * S + A] = x[A]; });
+        }
+    }
+    bin_tile_src<SP, float, T>(sample, v, rec, perm, rank, rpiece, cnt, start);
+    const int total = start[K];
+    for (int p = tid; p < total; p += blockDim.x) {
+        const int i = perm[p];
+        const int j = rpiece[i];
+        const Fold<S> f = unpack_rec<SP, float>(rec[i], v);
+        float val = 0.0f, g[S];
+        sfor<S>([&](auto A) { g[A] = 0.0f; });
+        sfor<K>([&](auto Jc) {
+            if (j == decltype(Jc)::value) eval_piece<SP, decltype(Jc)::value, GRAD, float>(f, v, val, g);
+        });
+        acc[i * NV] = val;
+        if constexpr (GRAD) sfor<S>([&](auto A) { acc[i * NV + 1 + A] = g[A]; });
+    }
+    __syncthreads();
+    for (int rl = tid; rl < RT; rl += blockDim.x) {
+        const int64_t pix = r0 + rl;
+        if (pix >= npix) break;
+        float val = 0.0f, g[S] = {0.0f, 0.0f, 0.0f};
+        for (int i = 0; i < steps; ++i) {
+            sfor<M>([&](auto Kc) {
+                const int it = Kc * T + rl * steps + i;
+                if (rpiece[it] >= 0) {
+                    val += acc[it * NV];
+                    if constexpr (GRAD) sfor<S>([&](auto A) { g[A] += acc[it * NV + 1 + A]; });
+                }
+            });
+        }
+        out[pix * (GRAD ? 4 : 1)] = val;
+        if constexpr (GRAD) sfor<S>([&](auto A) { out[pix * 4 + 1 + A] = g[A]; });
     }
 }
 

@@ -33,12 +33,16 @@ ib::DevVol<CT> make_vol(const void *c, const ibl::Layout &L)
 
 inline unsigned grid_for(int64_t n) { return (unsigned)((n + kTPB - 1) / kTPB); }
 
+// shared memory a CTA may use (opt-in maximum on sm_100 / sm_103)
+constexpr size_t kMaxSmem = 227 * 1024;
+
 // piece-binned kernel configurations: (tile of queries, threads per CTA)
 template <class CT, int MODE, int T, int NT>
 [[maybe_unused]] cudaError_t launch_binned_cfg(const float *pts, int64_t n, const void *c, const ibl::Layout &L,
                                                float *out, float *grad, const float *gout, cudaStream_t st)
 {
     constexpr size_t smem = ib::binned_smem_bytes<SP, MODE, T>();
+    static_assert(smem <= kMaxSmem, "binned tile must fit shared memory");
     auto kern = ib::k_eval_binned<SP, CT, MODE, T, NT>;
     static unsigned long long configured = 0;          // per device: the attribute is set once
     int dev = 0;
@@ -54,6 +58,15 @@ template <class CT, int MODE, int T, int NT>
     return cudaPeekAtLastError();
 }
 
+// queries per tile of the piece-binned kernels: 1024, or fewer when the tile's (query, coset)
+// items would not fit shared memory (many cosets, e.g. the 8 of D4)
+template <int MODE>
+constexpr int bin_tile()
+{
+    return ib::binned_smem_bytes<SP, MODE, 1024>() <= kMaxSmem ? 1024
+           : ib::binned_smem_bytes<SP, MODE, 512>() <= kMaxSmem ? 512 : 256;
+}
+
 template <class CT, int MODE>
 [[maybe_unused]] cudaError_t launch_eval_binned(const float *pts, int64_t n, const void *c, const ibl::Layout &L,
                                                 float *out, float *grad, const float *gout, cudaStream_t st)
@@ -62,7 +75,7 @@ template <class CT, int MODE>
         // INTERP_B300_BINCFG=small selects 256-query tiles on 128-thread CTAs (several CTAs per SM)
         const char *cfg = std::getenv("INTERP_B300_BINCFG");
         if (cfg && cfg[0] == 's') return launch_binned_cfg<CT, MODE, 256, 128>(pts, n, c, L, out, grad, gout, st);
-        return launch_binned_cfg<CT, MODE, 1024, 512>(pts, n, c, L, out, grad, gout, st);
+        return launch_binned_cfg<CT, MODE, bin_tile<MODE>(), 512>(pts, n, c, L, out, grad, gout, st);
     } else {
         return cudaErrorInvalidValue;
     }
@@ -79,14 +92,18 @@ cudaError_t launch_eval(const float *pts, int64_t n, const void *c, const ibl::L
 [[maybe_unused]] cudaError_t launch_adjoint(const float *pts, int64_t n, const float *gout, const ibl::Layout &L,
                                             float *dpad, cudaStream_t st)
 {
-    if constexpr (SP::S == 3) {
+    if constexpr (SP::S == 3 && SP::K < 4) {
         // blocks of sorted queries fit a shared-memory box: privatised sums (3-D)
         const unsigned grid = (unsigned)((n + ib::kAdjChunk - 1) / ib::kAdjChunk);
         ib::k_adjoint_priv<SP><<<grid, 256, 0, st>>>(pts, n, gout, make_vol<float>(nullptr, L), dpad);
     } else if constexpr (SP::K >= 4) {
-        // many pieces: sort each tile's items by piece first (no shared-memory box in 4-D)
-        constexpr int T = 1024, NT = 512;
+        // many pieces: sort each tile's items by piece first, then scatter with global atomics
+        // (divergence over the pieces costs more than the privatised box saves)
+        constexpr int T = ib::binned_adjoint_smem_bytes<SP, 1024>() <= kMaxSmem ? 1024
+                          : ib::binned_adjoint_smem_bytes<SP, 512>() <= kMaxSmem ? 512 : 256;
+        constexpr int NT = 512;
         constexpr size_t smem = ib::binned_adjoint_smem_bytes<SP, T>();
+        static_assert(smem <= kMaxSmem, "binned adjoint tile must fit shared memory");
         auto kern = ib::k_adjoint_binned<SP, T, NT>;
         static unsigned long long configured = 0;
         int dev = 0;
@@ -135,6 +152,31 @@ template <bool GRAD>
                                          float *pts_out, cudaStream_t st)
 {
     if constexpr (SP::S == 3) {
+        if constexpr (SP::K > 1) {
+            // multi-piece splines: whole rays per tile, samples binned by piece (as eval_launch:
+            // default for K >= 4, INTERP_B300_BINNED=0 / 1 forces the plain / binned kernel)
+            constexpr int T = bin_tile<GRAD ? 1 : 0>();
+            const char *bn = std::getenv("INTERP_B300_BINNED");
+            const bool want = bn ? bn[0] == '1' : SP::K >= 4;
+            if (want && rg.steps >= 1 && rg.steps <= T) {
+                constexpr size_t smem = ib::binned_smem_bytes<SP, GRAD ? 1 : 0, T>();
+                static_assert(smem <= kMaxSmem, "binned tile must fit shared memory");
+                auto kern = ib::k_rays_binned<SP, GRAD, T, 512>;
+                static unsigned long long configured = 0;
+                int dev = 0;
+                cudaError_t e = cudaGetDevice(&dev);
+                if (e != cudaSuccess) return e;
+                if (dev >= 64 || !(configured >> dev & 1ull)) {
+                    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    if (e != cudaSuccess) return e;
+                    if (dev < 64) configured |= 1ull << dev;
+                }
+                const int64_t rays = (int64_t)rg.width * rg.height;
+                const int rt = T / rg.steps;
+                kern<<<(unsigned)((rays + rt - 1) / rt), 512, smem, st>>>(rg, make_vol<float>(c, L), out, pts_out);
+                return cudaPeekAtLastError();
+            }
+        }
         const dim3 grid((rg.width + 15) / 16, (rg.height + 7) / 8);
         ib::k_rays<SP, GRAD><<<grid, 128, 0, st>>>(rg, make_vol<float>(c, L), out, pts_out);
         return cudaPeekAtLastError();
@@ -153,6 +195,7 @@ void IB_CAT(fill_, INTERP_SPLINE, _, INTERP_PART)(SplineOps &o)
     o.name = SP::NAME;
     o.s = SP::S;
     o.nxi = SP::NXI;
+    o.kind = SP::KIND;
     o.M = SP::M;
     o.D = SP::D;
     o.detl = SP::DETL;

@@ -20,6 +20,7 @@ using DbgFn = cudaError_t (*)(const float *, int64_t, const ibl::Layout &, int32
 struct SplineOps {
     const char *name = nullptr;
     int s = 0, nxi = 0, M = 0, D = 0, detl = 0, halo = 0, K = 0, deg = 0, nmon = 0;
+    int kind = 0;                // 0: box spline M_xi; n >= 1: Voronoi spline V_n (xi = 2 G)
     const int *xi = nullptr;     // s x nxi row-major
     const int *cosets = nullptr; // M x s
     double fma_value = 0, fma_grad = 0, lookups = 0;
@@ -46,7 +47,6 @@ enum Part { PART_VALUE = 0, PART_GRAD = 1, PART_PULL = 2, PART_MISC = 3 };
 
 namespace ibr {
 int batch_kind_3d(const char *name);
-int batch_kind_4d(const char *name);
 cudaError_t batch_grid_3d(int *grid);
 cudaError_t batch_launch_3d(const ibl::BatchVol *vols, int nvol, int64_t total_tiles, unsigned long long *counter,
                             int grid, cudaStream_t st);

@@ -17,8 +17,8 @@ from fractions import Fraction as Fr
 
 import numpy as np
 
-from .catalog import CATALOG
-from .pieces import analyse, horner_order, n_monomials
+from .catalog import CATALOG, VORONOI
+from .pieces import analyse, analyse_voronoi, horner_order, n_monomials, sec42_compression
 
 GEN_VERSION = 1
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -26,7 +26,23 @@ OUT_DIR = os.path.join(os.path.dirname(HERE), "csrc", "generated")
 # splines whose FP16 / BF16 coefficient-storage kernels are compiled (the 4-D spline's kernels are
 # large, so only its FP32 variant is built)
 HALF_STORAGE = {"bcc_linear", "bcc_quintic", "fcc_6dir", "cc_7dir", "bcc_quartic", "cc_linear_rd", "cc_voronoi1",
-                "cc_voronoi2", "cc_voronoi3"}
+                "cc_voronoi2", "cc_voronoi3", "bcc_voronoi1", "fcc_voronoi1"}
+# the 3-D splines compiled into the persistent batched kernel: few pieces and registers, so that
+# one of them does not lower the kernel's occupancy for the others
+BATCH_3D = {"bcc_linear", "bcc_quintic", "fcc_6dir", "cc_7dir", "bcc_quartic", "cc_linear_rd", "cc_voronoi1",
+            "cc_voronoi2"}
+# sigma has 2^Q entries: up to 64 of them are packed as 4-bit piece indices into 64-bit constants
+# (K <= 15), larger tables are byte arrays in device memory (Q <= 12)
+MAX_PIECES, MAX_PACKED, MAX_Q = 15, 64, 12
+
+
+def analyse_entry(name):
+    """The generator's tables for a built-in name (box spline or Voronoi spline)."""
+    if name in VORONOI:
+        L, gens, order = VORONOI[name]
+        return analyse_voronoi(name, L, gens, order)
+    L, xi = CATALOG[name]
+    return analyse(name, L, xi)
 
 
 def f32_hex(v) -> str:
@@ -90,12 +106,16 @@ def emit_struct(T, half_storage: bool = True) -> tuple[str, dict]:
     fma_grad = M * sum(w * (len(z) + hg) for w, z in zip(vols, nz_lists))
     lookups = M * sum(w * len(pc.sites) for w, pc in zip(vols, T.pieces))
 
-    L = []
+    L = [f"// ---- spline {T.name}"]
+    if T.r > MAX_PACKED:
+        # sigma as a byte table in device memory (read through the read-only cache)
+        L.append(f"static __device__ const unsigned char {T.name}_sigma_tab[{T.r}] = {_arr(T.sigma)};")
     L.append(f"struct {T.name} {{")
     L.append(f'    static constexpr const char* NAME = "{T.name}";')
     L.append(f"    static constexpr int S = {s}, NXI = {len(T.xi[0])}, M = {M}, D = {T.D}, DETL = {T.det_l};")
     L.append(f"    static constexpr int K = {K}, Q = {Q}, R = {T.r}, DEG = {T.degree}, NMON = {nmon}, HALO = {T.halo};")
     L.append(f"    static constexpr int NSMAX = {nsmax}, NNZMAX = {nnzmax}, FOLD = {T.fold};")
+    L.append(f"    static constexpr int KIND = {T.kind};  // 0: box spline M_XI; n: Voronoi spline V_n, XI = 2 G")
     L.append(f"    static constexpr bool HALF_STORAGE = {'true' if half_storage else 'false'};  // FP16/BF16 kernels built")
     L.append(f"    static constexpr int XI[S][NXI] = {_arr([_arr(r) for r in T.xi])};")
     L.append(f"    static constexpr int LMAT[S][S] = {_arr([_arr(r) for r in T.L])};")
@@ -107,6 +127,8 @@ def emit_struct(T, half_storage: bool = True) -> tuple[str, dict]:
         L.append("    static constexpr int PLANE_P[1][S] = {};")
         L.append("    static constexpr float PLANE_E[1] = {0.0f};")
     L.append(f"    static constexpr int SIGMA[R] = {_arr(T.sigma)};")
+    if T.r > MAX_PACKED:
+        L.append(f"    __device__ static unsigned sigma_at(unsigned q) {{ return __ldg(&{T.name}_sigma_tab[q]); }}")
     L.append(f"    static constexpr int NS[K] = {_arr([len(pc.sites) for pc in T.pieces])};")
     L.append(f"    static constexpr int NNZ[K] = {_arr([len(z) for z in nz_lists])};")
     L.append(f"    static constexpr float ANCHOR[K][S] = {_arr([_arr(pc.anchor, f32_hex) for pc in T.pieces])};")
@@ -148,9 +170,10 @@ def emit_struct(T, half_storage: bool = True) -> tuple[str, dict]:
     L.append(f"    static constexpr double FMA_VALUE = {fma_value!r}, FMA_GRAD = {fma_grad!r}, LOOKUPS = {lookups!r};")
     L.append("};")
 
-    meta = dict(name=T.name, s=s, L=T.L, xi=T.xi, det_l=T.det_l, D=T.D, cosets=T.cosets, fold=T.fold,
+    meta = dict(name=T.name, kind=T.kind, s=s, L=T.L, xi=T.xi, det_l=T.det_l, D=T.D, cosets=T.cosets, fold=T.fold,
                 degree=T.degree, n_monomials=nmon, halo=T.halo, r=T.r, sigma=T.sigma,
                 planes=[[list(p), str(e)] for p, e in T.planes],
+                r_sec42=sec42_compression([pc.code for pc in T.pieces], len(T.planes)),
                 pieces=[dict(anchor=[str(a) for a in pc.anchor], sites=pc.sites, code=pc.code,
                              nnz=len(z), volume_fraction=w,
                              vertices=[[str(a) for a in v] for v in pc.verts],
@@ -165,13 +188,29 @@ def emit_struct(T, half_storage: bool = True) -> tuple[str, dict]:
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=OUT_DIR)
-    ap.add_argument("names", nargs="*", default=list(CATALOG))
+    ap.add_argument("names", nargs="*", default=list(CATALOG) + list(VORONOI))
+    ap.add_argument("--update", nargs="+", default=None, metavar="NAME",
+                    help="re-analyse only these splines; take the others from the current output")
     args = ap.parse_args(argv)
     os.makedirs(args.out, exist_ok=True)
+    old_structs, old_metas = {}, {}
+    if args.update:
+        with open(os.path.join(args.out, "splines.h")) as f:
+            hdr_text = f.read()
+        for block in hdr_text.split("\n// ---- spline ")[1:]:
+            name = block.split("\n", 1)[0].strip()
+            old_structs[name] = "// ---- spline " + block[:block.index("\n};") + 3]
+        with open(os.path.join(args.out, "splines.json")) as f:
+            old_metas = json.load(f)["splines"]
     structs, metas = [], {}
     for name in args.names:
-        L, xi = CATALOG[name]
-        T = analyse(name, L, xi)
+        if args.update and name not in args.update and name in old_structs and name in old_metas:
+            structs.append(old_structs[name])
+            metas[name] = old_metas[name]
+            continue
+        T = analyse_entry(name)
+        if len(T.pieces) > MAX_PIECES or len(T.planes) > MAX_Q:
+            raise ValueError(f"{name}: {len(T.pieces)} pieces / {len(T.planes)} planes exceed the kernels' sigma table")
         text, meta = emit_struct(T, half_storage=name in HALF_STORAGE)
         structs.append(text)
         metas[name] = meta
@@ -201,11 +240,10 @@ def main(argv=None):
         "",
         "// X-macro over every built-in spline: X(struct name)",
         "#define INTERP_GEN_SPLINES(X) " + " ".join(f"X({n})" for n in args.names),
-        "// the same, split by dimension (the batched kernels are per dimension); comma-separated",
-        "#define INTERP_GEN_SPLINES_3D " + ", ".join(f"interp_gen::{n}" for n in args.names if metas[n]["s"] == 3),
-        "#define INTERP_GEN_SPLINES_4D " + ", ".join(f"interp_gen::{n}" for n in args.names if metas[n]["s"] == 4),
-        "#define INTERP_GEN_NAMES_3D " + ", ".join(f'"{n}"' for n in args.names if metas[n]["s"] == 3),
-        "#define INTERP_GEN_NAMES_4D " + ", ".join(f'"{n}"' for n in args.names if metas[n]["s"] == 4),
+        "// the 3-D splines of the persistent batched kernel (comma-separated); other handles of a",
+        "// batch run their own evaluation launch",
+        "#define INTERP_GEN_BATCH_3D " + ", ".join(f"interp_gen::{n}" for n in args.names if n in BATCH_3D),
+        "#define INTERP_GEN_BATCH_NAMES_3D " + ", ".join(f'"{n}"' for n in args.names if n in BATCH_3D),
         f'#define INTERP_GEN_DIGEST "{digest}"',
         "",
     ]

@@ -11,8 +11,9 @@ Steps (Horacsek & Alim, arXiv 2102.08514):
    change of variables (T, t, pi) of Sec. 4.3 becomes the per-query signed permutation S.
 4. Sub-regions: the mesh planes of Sec. 3 (hyperplanes spanned by (s-1)-subsets of Xi, through
    every sum of a subset of the columns, shifted by D Z^s) that cut the chamber; their cells are the
-   sub-regions of evaluation S_j (Sec. 4.1), identified branch-free by plane sign bits q and the
-   table sigma[q mod r] with r found by brute force (Sec. 4.2).
+   sub-regions of evaluation S_j (Sec. 4.1), identified branch-free by plane sign bits q and a
+   table sigma[q] (Sec. 4.2; uncompressed, so that codes of points on planes map to an adjacent
+   piece -- see _sigma_table).
 5. Per cell, the stencil C_0(S_j) (the coset sites whose shifted support covers the cell) and the
    explicit polynomial of phi(y - D g) for every stencil site g (the functions psi_j of Sec. 4.1).
    The polynomials are computed exactly (Fractions) by running de Boor's recurrence on polynomials
@@ -25,6 +26,7 @@ from __future__ import annotations
 
 import itertools
 import math
+import os
 from dataclasses import dataclass, field
 from fractions import Fraction as Fr
 from functools import lru_cache
@@ -91,8 +93,12 @@ def hyperplane_normal(vectors, s):
     not span a hyperplane); sign fixed so that the first nonzero entry is positive."""
     n = []
     for i in range(s):
-        sub = [[v[k] for k in range(s) if k != i] for v in vectors]
-        n.append((-1) ** i * det(sub) if s > 1 else 1)
+        sub = [[Fr(v[k]) for k in range(s) if k != i] for v in vectors]
+        n.append((-1) ** i * det(sub) if s > 1 else Fr(1))
+    den = 1
+    for a in n:
+        den = den * Fr(a).denominator // math.gcd(den, Fr(a).denominator)
+    n = [Fr(a) * den for a in n]
     g = 0
     for a in n:
         g = math.gcd(g, abs(int(a)))
@@ -310,22 +316,101 @@ class SplineTables:
     fold: int             # 2: signed permutations, 0: none
     degree: int
     planes: list          # (p: tuple of ints, e: Fraction) in the folded frame
-    r: int
-    sigma: list           # sigma[q mod r] -> piece index (-1 unused)
+    r: int                # sigma's length, 2^Q (the table is indexed by q directly)
+    sigma: list           # sigma[q] -> piece index
     pieces: list
     halo: int             # max |g_a| over all stencil sites (grid units)
     lookups: int = 0      # coefficient reads per query (all cosets)
+    kind: int = 0         # 0: box spline M_Xi; n >= 1: Voronoi spline V_n (xi records 2 G)
 
 
-def _zonotope_halfwidths(cols, normals):
-    return {p: Fr(sum(abs(sum(p[a] * c[a] for a in range(len(p)))) for c in cols), 2) for p in normals}
+@dataclass(frozen=True)
+class Term:
+    """One summand w * M_cols(x + c) of phi (cols: direction vectors as tuples of Fractions)."""
+    w: Fr
+    cols: tuple
+    c: tuple
+
+
+def box_spline_terms(xi, det_l):
+    """phi = |det L| M_Xi(x + sum(Xi)/2), the centred box spline scaled to a partition of unity."""
+    s, n = len(xi), len(xi[0])
+    cols = tuple(tuple(Fr(xi[a][j]) for a in range(s)) for j in range(n))
+    return [Term(Fr(det_l), cols, tuple(sum(c[a] for c in cols) / 2 for a in range(s)))]
+
+
+def zonotope_tiling(gens):
+    """Tiles of the zonotope Z(G) = sum_j [0, g_j] by parallelepipeds: a list of (B, z_B, |det B|)
+    over the bases B of G with Z(G) = union of z_B + B[0,1)^s (disjoint up to boundaries).
+
+    The tiles are the lower facets of the zonotope of the lifted generators (g_j, h_j) for generic
+    heights h_j, projected back: the facet spanned by B has the normal (-a, 1) with a . g_b = h_b
+    on B, and its offset is the sum of the g_j (j not in B) with h_j < a . g_j."""
+    s, m = len(gens[0]), len(gens)
+    for k in itertools.count(2):
+        hts = [Fr((j + 1) ** k) for j in range(m)]
+        tiles = []
+        generic = True
+        for B in itertools.combinations(range(m), s):
+            GB = [[Fr(gens[b][a]) for b in B] for a in range(s)]
+            dB = det(GB)
+            if dB == 0:
+                continue
+            a_ = solve([[Fr(gens[b][a]) for a in range(s)] for b in B], [hts[b] for b in B])
+            z = [Fr(0)] * s
+            for j in range(m):
+                if j in B:
+                    continue
+                d = hts[j] - sum(a_[a] * gens[j][a] for a in range(s))
+                if d == 0:
+                    generic = False
+                    break
+                if d < 0:
+                    z = [z[a] + gens[j][a] for a in range(s)]
+            if not generic:
+                break
+            tiles.append((B, tuple(z), abs(dB)))
+        if generic:
+            return tiles
+
+
+def voronoi_terms(gens, order, det_l):
+    """phi = |det L| V_order with V_0 = chi (1/|det L| on the Voronoi region), V_n = V_0 * V_{n-1}
+    (Sec. 3), for a Voronoi region that is the centred zonotope of the generators G.
+
+    V_0 = 1/|det L| sum_B |det B| M_B(x + sum(G)/2 - z_B) over the tiles (B, z_B) of Z(G); the
+    (order+1)-fold convolution expands by the multinomial theorem into box splines of the
+    concatenated bases (Sec. 3: convolving box splines concatenates their direction matrices and
+    adds their shifts).  Equal (directions, shift) pairs are merged."""
+    s = len(gens[0])
+    gens = [tuple(Fr(v) for v in g) for g in gens]
+    tiles = zonotope_tiling(gens)
+    half = [sum(g[a] for g in gens) / 2 for a in range(s)]
+    acc = {}
+    for combo in itertools.combinations_with_replacement(range(len(tiles)), order + 1):
+        mult = math.factorial(order + 1)
+        for i in set(combo):
+            mult //= math.factorial(combo.count(i))
+        w = Fr(mult) * Fr(det_l) / Fr(det_l) ** (order + 1)
+        for i in combo:
+            w *= tiles[i][2]
+        cols = tuple(sorted(gens[b] for i in combo for b in tiles[i][0]))
+        c = tuple(sum(half[a] - tiles[i][1][a] for i in combo) for a in range(s))
+        acc[(cols, c)] = acc.get((cols, c), 0) + w
+    return [Term(w, cols, c) for (cols, c), w in sorted(acc.items())]
+
+
+def _canon_dir(v):
+    for a in v:
+        if a != 0:
+            return tuple(v) if a > 0 else tuple(-b for b in v)
+    return tuple(v)
 
 
 def analyse(name, L, xi, anchor_den=64, verbose=False):
     """Run the analysis for phi = |det L| M_Xi(. + sum(Xi)/2) on the lattice L Z^s."""
     s = len(xi)
-    n = len(xi[0])
-    cols = [tuple(int(xi[a][j]) for a in range(s)) for j in range(n)]
+    cols = [tuple(int(xi[a][j]) for a in range(s)) for j in range(len(xi[0]))]
     if rank(cols, s) != s:
         raise ValueError("Xi must have rank s")
     D, cosets, det_l = coset_structure(L)
@@ -334,24 +419,52 @@ def analyse(name, L, xi, anchor_den=64, verbose=False):
         if any(sum(Linv[i][j] * c[j] for j in range(s)).denominator != 1 for i in range(s)):
             raise ValueError("L^{-1} Xi must be integer")
     fold = 2 if signed_permutation_invariant(xi) else 0
-    centre = [Fr(sum(c[a] for c in cols), 2) for a in range(s)]
-    degree = n - s
+    return analyse_terms(name, L, box_spline_terms(xi, det_l), fold, [list(r) for r in xi], 0, anchor_den, verbose)
 
-    # mesh plane normals and offsets (Sec. 3, the fine mesh Gamma)
-    normals = set()
-    for sub in itertools.combinations(cols, s - 1):
-        p = hyperplane_normal(list(sub), s)
-        if p is not None:
-            normals.add(p)
-    normals = sorted(normals)
+
+def analyse_voronoi(name, L, gens, order, anchor_den=64, verbose=False):
+    """Run the analysis for phi = |det L| V_order on L Z^s, the Voronoi region of L being the
+    centred zonotope of the generators gens (rational vectors).  The recorded direction matrix
+    is 2 G (integers for the BCC and FCC regions)."""
+    s = len(L)
+    D, cosets, det_l = coset_structure(L)
+    G = [[Fr(v) for v in g] for g in gens]
+    if sum(t[2] for t in zonotope_tiling(G)) != det_l:
+        raise ValueError("the zonotope's volume must be |det L| (a Voronoi region of L)")
+    xi2 = [[int(2 * g[a]) for g in G] for a in range(s)]
+    fold = 2 if signed_permutation_invariant(xi2) else 0
+    return analyse_terms(name, L, voronoi_terms(G, order, det_l), fold, xi2, order, anchor_den, verbose)
+
+
+def analyse_terms(name, L, terms, fold, xi_record, kind, anchor_den=64, verbose=False):
+    """The analysis of Sec. 4 for phi = sum_t w_t M_{cols_t}(x + c_t) on the lattice L Z^s."""
+    s = len(L)
+    D, cosets, det_l = coset_structure(L)
+    degree = len(terms[0].cols) - s
+    if any(len(t.cols) - s != degree for t in terms):
+        raise ValueError("all terms must have the same degree")
+
+    # mesh plane normals and offsets (Sec. 3, the fine mesh Gamma) of every term
     offsets = {}
-    for p in normals:
-        dots = [sum(p[a] * c[a] for a in range(s)) for c in cols]
-        sums = {0}
-        for dv in dots:
-            sums |= {x + dv for x in sums}
-        pc = sum(p[a] * centre[a] for a in range(s))
-        offsets[p] = sorted({Fr(x) - pc for x in sums})
+    term_normals = []
+    for t in terms:
+        dirs = sorted({_canon_dir(c) for c in t.cols})
+        tn = set()
+        for sub in itertools.combinations(dirs, s - 1):
+            p = hyperplane_normal(list(sub), s)
+            if p is not None:
+                tn.add(p)
+        tn = sorted(tn)
+        term_normals.append(tn)
+        for p in tn:
+            sums = {Fr(0)}
+            for c in t.cols:
+                dv = sum(p[a] * c[a] for a in range(s))
+                sums |= {x + dv for x in sums}
+            pc = sum(p[a] * t.c[a] for a in range(s))
+            offsets.setdefault(p, set()).update(x - pc for x in sums)
+    normals = sorted(offsets)
+    offsets = {p: sorted(v) for p, v in offsets.items()}
 
     # region of evaluation, folded
     half = Fr(D, 2)
@@ -390,67 +503,149 @@ def analyse(name, L, xi, anchor_den=64, verbose=False):
             nxt.extend(split(c, p, e, s, idx))
         cells = nxt
     if verbose:
-        print(f"{name}: s={s} n={n} D={D} cosets={len(cosets)} fold={fold} Q={len(planes)} cells={len(cells)}")
+        print(f"{name}: s={s} terms={len(terms)} D={D} cosets={len(cosets)} fold={fold} Q={len(planes)} "
+              f"cells={len(cells)}")
 
-    halfw = _zonotope_halfwidths(cols, normals)
-    bbox = [Fr(sum(abs(c[a]) for c in cols), 2) for a in range(s)]
+    # per term: support half-widths along its facet normals, support centre, bounding box
+    geo = []
+    for t, tn in zip(terms, term_normals):
+        hw = {p: sum(abs(sum(p[a] * c[a] for a in range(s))) for c in t.cols) / 2 for p in tn}
+        mid = [sum(c[a] for c in t.cols) / 2 - t.c[a] for a in range(s)]
+        lo = [sum(min(0, c[a]) for c in t.cols) - t.c[a] for a in range(s)]
+        hi = [sum(max(0, c[a]) for c in t.cols) - t.c[a] for a in range(s)]
+        geo.append((tn, hw, mid, lo, hi))
+    blo = [min(g[3][a] for g in geo) for a in range(s)]
+    bhi = [max(g[4][a] for g in geo) for a in range(s)]
+    groups = {}
+    for ti, t in enumerate(terms):
+        groups.setdefault(t.cols, []).append(ti)
 
-    pieces = []
-    for c in cells:
-        z = c.interior_point()
-        # stencil: coset sites D g whose open support contains the cell (test at an interior point)
-        rng = [range(math.floor((z[a] - bbox[a]) / D), math.ceil((z[a] + bbox[a]) / D) + 1) for a in range(s)]
-        sites = []
-        for g in itertools.product(*rng):
-            w = [z[a] - D * g[a] for a in range(s)]
-            if all(abs(sum(p[a] * w[a] for a in range(s))) < halfw[p] for p in normals):
-                sites.append(list(g))
-        polys = _piece_polynomials(cols, s, det_l, centre, D, z, sites)
-        # expansion point: among the cell's vertices and its (dyadic-rounded) centroid, the one
-        # that leaves the fewest nonzero coefficients (fewest FMAs), then the smallest ones
-        cands = [list(v) for v in c.verts] + [[Fr(round(z[a] * anchor_den), anchor_den) for a in range(s)]]
-        best = None
-        for cand in cands:
-            if any((2 * anchor_den * v).denominator != 1 for v in cand):
-                continue                  # keep anchors exact in FP32
-            shifted = [P.taylor_shift(cand) for P in polys]
-            key = (sum(len(P.c) for P in shifted), max(abs(v) for P in shifted for v in P.c.values()))
-            if best is None or key < best[0]:
-                best = (key, cand, shifted)
-        _, anchor, polys = best
-        code = sum((c.signs[i] << i) for i in range(len(planes)))
-        pieces.append(Piece(anchor, sites, polys, code, c.verts, c.ineqs))
+    ctx = (s, D, terms, geo, groups, blo, bhi, anchor_den, len(planes))
+    if len(terms) > 32 and len(cells) > 1:
+        # many terms: the cells are independent, analyse them in worker processes
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(min(len(cells), os.cpu_count() or 1), mp_context=mp.get_context("fork"),
+                                 initializer=_set_ctx, initargs=(ctx,)) as ex:
+            pieces = list(ex.map(_cell_piece, cells))
+    else:
+        _set_ctx(ctx)
+        pieces = [_cell_piece(c) for c in cells]
 
     codes = [pc.code for pc in pieces]
     Q = len(planes)
-
-    def nearest(q):
-        # a sign code no cell has (rounding near where several planes meet): the piece whose code
-        # differs in the fewest plane bits, which is a piece meeting at that corner
-        return min(range(len(codes)), key=lambda j: (bin(q ^ codes[j]).count("1"), j))
-
-    if Q <= 4:
-        # small Q: index sigma by q directly (r = 2^Q), every code mapped to a real piece
-        r = 1 << Q
-        sigma = [nearest(q) for q in range(r)]
-    else:
-        # Sec. 4.2: compress [0, 2^Q) to [0, r) by q mod r, r the smallest value separating the
-        # cells' codes (brute force)
-        r = next(r for r in range(len(codes), 1 << Q) if len({q % r for q in codes}) == len(codes))
-        sigma = [-1] * r
-        for j, q in enumerate(codes):
-            sigma[q % r] = j
-        for i in range(r):
-            if sigma[i] < 0:
-                sigma[i] = nearest(i)
+    sigma = _sigma_table(cells, chamber, planes, codes, s)
+    r = 1 << Q
     halo = max((abs(g[a]) for pc in pieces for g in pc.sites for a in range(s)), default=0)
     lookups = max(len(pc.sites) for pc in pieces) * len(cosets)
-    return SplineTables(name, s, [list(r_) for r_ in L], [list(r_) for r_ in xi], det_l, D, cosets,
-                        fold, degree, planes, r, sigma, pieces, halo, lookups)
+    return SplineTables(name, s, [list(r_) for r_ in L], xi_record, det_l, D, cosets,
+                        fold, degree, planes, r, sigma, pieces, halo, lookups, kind)
 
 
-def _piece_polynomials(cols, s, det_l, centre, D, z, sites):
-    """Exact polynomials of phi(y - D g), y in the cell around the interior point z, for every g.
+def sec42_compression(codes, Q):
+    """Sec. 4.2's r: the smallest r with q mod r distinct over the cells' codes (brute force)."""
+    return next(r for r in range(len(codes), (1 << Q) + 1) if len({q % r for q in codes}) == len(codes))
+
+
+def _sigma_table(cells, chamber, planes, codes, s):
+    """sigma[q] for every plane sign code q in [0, 2^Q).
+
+    A query exactly on one or more planes (or where FP32 rounding flips a bit next to them) gets
+    a code that no open cell has.  Any piece whose closure contains the query gives the right
+    value (the spline is continuous), so such a code q is mapped through its closed region
+    R_q = {y in the chamber : p_i . y >= e_i where bit i is set, <= e_i where it is not}: if R_q
+    is not empty, to the first cell whose closure contains a relative-interior point of R_q
+    (exact rational vertices); if it is empty, like the code at the smallest Hamming distance
+    whose region is not.  This is why the kernels index sigma by q directly: Sec. 4.2's
+    compression to q mod r keeps the cells' own codes apart but folds these codes onto
+    unrelated pieces."""
+    Q = len(planes)
+    table = [-1] * (1 << Q)
+    for j, q in enumerate(codes):
+        table[q] = j
+    if Q:
+        import numpy as np
+        from scipy.optimize import linprog
+        A0 = [list(map(float, a)) for a, _ in chamber]
+        b0 = [float(b) for _, b in chamber]
+        for q in range(1 << Q):
+            if table[q] >= 0:
+                continue
+            ineqs = list(chamber)
+            for i, (p, e) in enumerate(planes):
+                ineqs.append((list(p), e) if not (q >> i) & 1 else ([-x for x in p], -e))
+            A = A0 + [list(map(float, a)) for a, _ in ineqs[len(chamber):]]
+            b = b0 + [float(bb) for _, bb in ineqs[len(chamber):]]
+            lp = linprog(np.zeros(s), A_ub=np.array(A), b_ub=np.array(b) + 1e-9, bounds=[(None, None)] * s,
+                         method="highs")
+            if lp.status != 0:
+                continue
+            vs = vertices(ineqs, s)
+            if not vs:
+                continue
+            c = [sum(v[a] for v in vs) / len(vs) for a in range(s)]
+            for j, cell in enumerate(cells):
+                if all(sum(a[k] * c[k] for k in range(s)) <= bb for a, bb in cell.ineqs):
+                    table[q] = j
+                    break
+    filled = [q for q in range(1 << Q) if table[q] >= 0]
+    for q in range(1 << Q):
+        if table[q] < 0:
+            table[q] = table[min(filled, key=lambda f: (bin(q ^ f).count("1"), f))]
+    return table
+
+
+_CTX = None
+
+
+def _set_ctx(ctx):
+    global _CTX
+    _CTX = ctx
+
+
+def _cell_piece(c):
+    """Stencil, exact polynomials and anchor of one cell (Sec. 4.1, the psi_j of S_j)."""
+    s, D, terms, geo, groups, blo, bhi, anchor_den, Q = _CTX
+    z = c.interior_point()
+    # stencil: coset sites D g with z - D g in the open support of some term
+    rng = [range(math.floor((z[a] - bhi[a]) / D), math.ceil((z[a] - blo[a]) / D) + 1) for a in range(s)]
+    polys = {}
+    for cols, tis in groups.items():
+        per_site = []
+        for g in itertools.product(*rng):
+            w = [z[a] - D * g[a] for a in range(s)]
+            hit = []
+            for ti in tis:
+                tn, hw, mid, _, _ = geo[ti]
+                if all(abs(sum(p[a] * (w[a] - mid[a]) for a in range(s))) < hw[p] for p in tn):
+                    hit.append(ti)
+            if hit:
+                per_site.append((g, [(terms[ti].w, terms[ti].c) for ti in hit]))
+        if not per_site:
+            continue
+        for (g, _), P in zip(per_site, _piece_polynomials(cols, s, D, z, per_site)):
+            polys[g] = polys[g].add(P) if g in polys else P
+    sites = [list(g) for g in sorted(polys) if not polys[g].is_zero()]
+    polys = [polys[tuple(g)] for g in sites]
+    # expansion point: among the cell's vertices and its (dyadic-rounded) centroid, the one
+    # that leaves the fewest nonzero coefficients (fewest FMAs), then the smallest ones
+    cands = [list(v) for v in c.verts] + [[Fr(round(z[a] * anchor_den), anchor_den) for a in range(s)]]
+    best = None
+    for cand in cands:
+        if any((2 * anchor_den * v).denominator != 1 for v in cand):
+            continue                  # keep anchors exact in FP32
+        shifted = [P.taylor_shift(cand) for P in polys]
+        key = (sum(len(P.c) for P in shifted), max(abs(v) for P in shifted for v in P.c.values()))
+        if best is None or key < best[0]:
+            best = (key, cand, shifted)
+    _, anchor, polys = best
+    code = sum((c.signs[i] << i) for i in range(Q))
+    return Piece(anchor, sites, polys, code, c.verts, c.ineqs)
+
+
+def _piece_polynomials(cols, s, D, z, sites):
+    """Exact polynomials of sum_t w_t M_cols(y - D g + c_t), y in the cell around the interior
+    point z, for every entry (g, [(w_t, c_t), ...]) of sites (terms sharing the directions cols).
 
     M_{Xi'}(y + v) is computed by de Boor's recurrence on polynomials in y with t supported on a
     basis B of Xi' (t_xi = 0 off B), so (n'-s) M = sum_{xi in B} [M1 + t_xi (M0 - M1)]
@@ -529,7 +724,10 @@ def _piece_polynomials(cols, s, det_l, centre, D, z, sites):
 
     full = (1 << n) - 1
     out = []
-    for g in sites:
-        v = tuple(Fr(centre[a]) - D * g[a] for a in range(s))
-        out.append(M(full, v).scale(det_l))
+    for g, wcs in sites:
+        acc = Poly()
+        for w, c in wcs:
+            v = tuple(Fr(c[a]) - D * g[a] for a in range(s))
+            acc = acc.add(M(full, v).scale(w))
+        out.append(acc)
     return out

@@ -1,6 +1,7 @@
 """Helpers shared by the GPU parity tests (test code only)."""
 import json
 import os
+from fractions import Fraction
 
 import numpy as np
 
@@ -25,6 +26,49 @@ def spline_setup(name):
     xi = np.asarray(sp.xi)
     detl = abs(round(np.linalg.det(np.asarray(lat.L, dtype=float))))
     return sp, lat, xi, detl
+
+
+class OracleSpline:
+    """The oracle's basis for a built-in spline name: oracle.Spline for a box spline,
+    oracle.VoronoiSpline for a Voronoi spline (generators = xi / 2), one interface."""
+
+    def __init__(self, name):
+        import oracle
+        sp, lat, xi, detl = spline_setup(name)
+        if sp.order:
+            gens = [tuple(Fraction(int(v), 2) for v in col) for col in xi.T]
+            self.v, self.sp = oracle.VoronoiSpline(lat.L, gens, sp.order), None
+        else:
+            self.v, self.sp = None, oracle.Spline(xi, detl)
+        self.halfwidth = (self.v or self.sp).halfwidth
+
+    def phi(self, z, grad=False):
+        return (self.v or self.sp).phi(z, grad=grad)
+
+    def eval_sum(self, D, cosets, c, pts, grad=False):
+        import oracle
+        c = np.asarray(c, dtype=np.float64)
+        pts = np.asarray(pts, dtype=np.float64)
+        if self.v is not None:
+            return self.v.eval_sum(D, cosets, c, pts, grad=grad)
+        return oracle.eval_sum(self.sp, D, cosets, c, pts, grad=grad)
+
+    def adjoint(self, D, cosets, shape, pts, g):
+        import oracle
+        pts = np.asarray(pts, dtype=np.float64)
+        g = np.asarray(g, dtype=np.float64)
+        if self.v is not None:
+            return self.v.adjoint(D, cosets, shape, pts, g)
+        return oracle.adjoint(self.sp, D, cosets, shape, pts, g)
+
+
+def make_interpolator(name, dims, storage="f32"):
+    """The CUDA path's handle: by (L, Xi) for a box spline, by name for a Voronoi spline."""
+    from paper_2102_08514_b300.binding import Interpolator
+    sp, lat, xi, detl = spline_setup(name)
+    if sp.order:
+        return Interpolator.named(name, dims, storage)
+    return Interpolator(np.asarray(lat.L), xi, dims, storage)
 
 
 def mixed_points(name, dims, n, seed, outside=True):
@@ -54,7 +98,7 @@ def grad_bound(name, pts):
     """G = max over pts of sum_n |grad phi(x - n)|_inf, from the oracle (at least 1)."""
     import oracle
     sp, lat, xi, detl = spline_setup(name)
-    o = oracle.Spline(xi, detl)
+    o = OracleSpline(name)
     G = 1.0
     for x in np.asarray(pts, dtype=np.float64):
         sites = oracle.lattice_sites(lat.L, x - o.halfwidth - 1, x + o.halfwidth + 1)

@@ -20,13 +20,17 @@ import pytest
 import oracle
 from synth import LATTICES, SPLINES
 
+from _gpu_common import OracleSpline
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 GEN = os.path.join(ROOT, "paper_2102_08514_b300", "csrc", "generated")
-NAMES = ["bcc_linear", "bcc_quintic", "fcc_6dir", "cc_7dir", "d4s_8dir", "bcc_quartic", "cc_linear_rd", "cc_voronoi1",
-         "cc_voronoi2", "cc_voronoi3"]
+NAMES = ["bcc_linear", "bcc_quintic", "fcc_6dir", "cc_7dir", "d4s_8dir", "d4_8dir", "bcc_quartic", "cc_linear_rd", "cc_voronoi1",
+         "cc_voronoi2", "cc_voronoi3", "bcc_voronoi1", "fcc_voronoi1", "fcc_voronoi2", "bcc_voronoi2"]
 # Table 1 '# Lookups' (and Sec. 5.2 for D4*)
-TABLE1_LOOKUPS = {"bcc_linear": 4, "bcc_quintic": 32, "fcc_6dir": 16, "cc_7dir": 53, "d4s_8dir": 60, "bcc_quartic": 30,
-                  "cc_linear_rd": 16, "cc_voronoi1": 8, "cc_voronoi2": 27, "cc_voronoi3": 64}
+TABLE1_LOOKUPS = {"bcc_linear": 4, "bcc_quintic": 32, "fcc_6dir": 16, "cc_7dir": 53, "d4s_8dir": 60, "d4_8dir": 240,
+                  "bcc_quartic": 30,
+                  "cc_linear_rd": 16, "cc_voronoi1": 8, "cc_voronoi2": 27, "cc_voronoi3": 64, "bcc_voronoi1": 8,
+                  "bcc_voronoi2": 27, "fcc_voronoi1": 8, "fcc_voronoi2": 27}
 
 
 @pytest.fixture(scope="module")
@@ -81,9 +85,9 @@ def test_tables_match_the_oracle(tables, name):
     rng = np.random.default_rng(7)
     N = 6
     c = rng.uniform(-1, 1, (len(lat.cosets),) + (N,) * s)
-    npts = 40 if s == 4 or tab["degree"] > 6 else 80
+    npts = 40 if s == 4 or tab["degree"] > 6 or name == "bcc_voronoi2" else 80
     pts = (np.round(rng.uniform(0, lat.D * N, (npts, s)) * 2 ** 12) / 2 ** 12)
-    ref = oracle.eval_sum(oracle.Spline(np.asarray(sp.xi), tab["det_l"]), lat.D, lat.cosets, c, pts)
+    ref = OracleSpline(name).eval_sum(lat.D, lat.cosets, c, pts)
     got = np.array([float(table_eval(tab, c, x)) for x in pts])
     assert np.abs(got - ref).max() < 1e-12
 
@@ -129,6 +133,22 @@ def test_header_matches_a_fresh_generator_run(tables):
         assert meta["sigma"] == tables[name]["sigma"]
     names = re.search(r"#define INTERP_GEN_SPLINES\(X\) (.*)", hdr).group(1)
     assert re.findall(r"X\((\w+)\)", names) == NAMES
+
+
+def test_voronoi_expansion_sizes_are_the_papers():
+    # Sec. 3: the BCC Voronoi region is 16 constant box splines, V_1 a sum of 136 box splines and
+    # V_2 of 816 (before equal terms are merged); the FCC region (rhombic dodecahedron) is 4
+    from math import comb
+    from paper_2102_08514_b300.gen.catalog import G_BCC_VORONOI, G_FCC_VORONOI
+    from paper_2102_08514_b300.gen.pieces import voronoi_terms, zonotope_tiling
+    nb = len(zonotope_tiling([tuple(Fraction(v) for v in g) for g in G_BCC_VORONOI]))
+    assert nb == 16 and comb(nb + 1, 2) == 136 and comb(nb + 2, 3) == 816
+    assert len(zonotope_tiling([tuple(Fraction(v) for v in g) for g in G_FCC_VORONOI])) == 4
+    for G, det_l in ((G_BCC_VORONOI, 4), (G_FCC_VORONOI, 2)):
+        for order in (1, 2):
+            terms = voronoi_terms(G, order, det_l)
+            assert sum(t.w for t in terms) == det_l          # each M integrates to 1
+            assert all(len(t.cols) == 3 * (order + 1) for t in terms)
 
 
 def test_fold_requires_the_symmetry():

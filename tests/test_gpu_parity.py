@@ -13,23 +13,24 @@ import pytest
 import oracle
 from synth import LATTICES, SPLINES, WORKLOADS, coefficients, interior_box, make_rng, uniform_points
 
-from _gpu_common import VALUE_TOL, grad_bound, mixed_points, require_cuda, spline_setup, tables
+from _gpu_common import (VALUE_TOL, OracleSpline, grad_bound, make_interpolator, mixed_points, require_cuda,
+                         spline_setup, tables)
 
 pytestmark = pytest.mark.gpu
 
-SPLINES_ALL = ["bcc_linear", "bcc_quintic", "fcc_6dir", "cc_7dir", "d4s_8dir", "bcc_quartic", "cc_linear_rd",
-               "cc_voronoi1", "cc_voronoi2", "cc_voronoi3"]
+SPLINES_ALL = ["bcc_linear", "bcc_quintic", "fcc_6dir", "cc_7dir", "d4s_8dir", "d4_8dir", "bcc_quartic", "cc_linear_rd",
+               "cc_voronoi1", "cc_voronoi2", "cc_voronoi3", "bcc_voronoi1", "bcc_voronoi2", "fcc_voronoi1",
+               "fcc_voronoi2"]
 # small cases the oracle finishes in seconds, spanning several thread blocks and a ragged tail
 SMALL = {"bcc_linear": (12, 4133), "bcc_quintic": (12, 2085), "fcc_6dir": (10, 3011), "cc_7dir": (14, 2107),
-         "d4s_8dir": (7, 1093), "bcc_quartic": (12, 2091), "cc_linear_rd": (14, 3003), "cc_voronoi1": (14, 4099),
-         "cc_voronoi2": (14, 2049), "cc_voronoi3": (12, 389)}
+         "d4s_8dir": (7, 1093), "d4_8dir": (6, 517), "bcc_quartic": (12, 2091), "cc_linear_rd": (14, 3003), "cc_voronoi1": (14, 4099),
+         "cc_voronoi2": (14, 2049), "cc_voronoi3": (12, 389), "bcc_voronoi1": (12, 4111),
+         "bcc_voronoi2": (10, 397), "fcc_voronoi1": (10, 3079), "fcc_voronoi2": (10, 1031)}
 
 
 def _interp(name, dims, storage="f32"):
     torch = require_cuda()
-    from paper_2102_08514_b300.binding import Interpolator
-    sp, lat, xi, detl = spline_setup(name)
-    return torch, Interpolator(np.asarray(lat.L), xi, dims, storage)
+    return torch, make_interpolator(name, dims, storage)
 
 
 def _coeffs(name, dims, seed):
@@ -48,7 +49,7 @@ def test_value_parity_small(name):
     itp.set_coeffs(torch.from_numpy(c).cuda())
     pts = mixed_points(name, dims, nq, 2)
     got = itp.eval(torch.from_numpy(pts).cuda()).cpu().numpy()
-    ref = oracle.eval_sum(oracle.Spline(xi, detl), lat.D, lat.cosets, c.astype(np.float64), pts.astype(np.float64))
+    ref = OracleSpline(name).eval_sum(lat.D, lat.cosets, c, pts)
     err = np.abs(got - ref)
     assert err.max() <= VALUE_TOL * np.abs(c).max(), (err.max(), int(err.argmax()))
 
@@ -95,8 +96,7 @@ def test_gradient_parity(name):
     lo, hi = interior_box(name, dims)
     pts = uniform_points(make_rng(5, 0), nq // 2, lo, hi)
     val, grad = itp.eval_grad(torch.from_numpy(pts).cuda())
-    sp_o = oracle.Spline(xi, detl)
-    ref_v, ref_g = oracle.eval_sum(sp_o, lat.D, lat.cosets, c.astype(np.float64), pts.astype(np.float64), grad=True)
+    ref_v, ref_g = OracleSpline(name).eval_sum(lat.D, lat.cosets, c, pts, grad=True)
     G = grad_bound(name, pts[:32])
     cmax = np.abs(c).max()
     assert np.abs(val.cpu().numpy() - ref_v).max() <= VALUE_TOL * cmax
@@ -117,9 +117,9 @@ def test_adjoint_parity(name):
     dpre = make_rng(8, 0).uniform(-1, 1, shape).astype(np.float32)      # accumulated into (+=)
     dc = torch.from_numpy(dpre.copy()).cuda()
     itp.backward(torch.from_numpy(pts).cuda(), torch.from_numpy(g).cuda(), dc)
-    sp_o = oracle.Spline(xi, detl)
-    ref = oracle.adjoint(sp_o, lat.D, lat.cosets, shape, pts.astype(np.float64), g.astype(np.float64))
-    bound = oracle.adjoint(sp_o, lat.D, lat.cosets, shape, pts.astype(np.float64), np.abs(g).astype(np.float64))
+    sp_o = OracleSpline(name)
+    ref = sp_o.adjoint(lat.D, lat.cosets, shape, pts, g)
+    bound = sp_o.adjoint(lat.D, lat.cosets, shape, pts, np.abs(g))
     err = np.abs(dc.cpu().numpy() - dpre - ref)
     assert np.all(err <= 4e-6 * bound + 1e-7), (err.max(), bound.max())
 
@@ -232,7 +232,7 @@ def test_full_size_headline_workload_sampled():
     assert np.abs(grad.cpu().numpy()[idx] - ref_g).max() <= VALUE_TOL * cmax * G
 
 
-@pytest.mark.parametrize("name", ["fcc_6dir", "d4s_8dir"])
+@pytest.mark.parametrize("name", ["fcc_6dir", "d4s_8dir", "d4_8dir", "bcc_voronoi1", "fcc_voronoi2"])
 def test_piece_binned_kernel_equals_plain_kernel(name, monkeypatch):
     # multi-piece splines run a piece-binned kernel by default; INTERP_B300_BINNED=0 selects the
     # plain one: same sums in the same order, so the results agree exactly
@@ -254,6 +254,27 @@ def test_piece_binned_kernel_equals_plain_kernel(name, monkeypatch):
         res.append((v, v2, gr, dp))
     for a, b in zip(*res):
         assert torch.equal(torch.nan_to_num(a, nan=7.0), torch.nan_to_num(b, nan=7.0))
+
+
+def test_named_creation_matches_lattice_and_directions():
+    # interp_create_named reaches the same tables as interp_create for a box spline; a Voronoi
+    # spline's recorded generators never match a direction-matrix request
+    torch = require_cuda()
+    from paper_2102_08514_b300.binding import Interpolator, InterpError
+    dims = (9, 10, 11)
+    a = _interp("fcc_6dir", dims)[1]
+    b = Interpolator.named("fcc_6dir", dims)
+    c = _coeffs("fcc_6dir", dims, 21)
+    a.set_coeffs(torch.from_numpy(c).cuda())
+    b.set_coeffs(torch.from_numpy(c).cuda())
+    pts = torch.from_numpy(mixed_points("fcc_6dir", dims, 3000, 22)).cuda()
+    assert torch.equal(torch.nan_to_num(a.eval(pts), nan=7.0), torch.nan_to_num(b.eval(pts), nan=7.0))
+    assert b.info.kind == 0 and Interpolator.named("bcc_voronoi2", dims).info.kind == 2
+    sp, lat, xi, _ = spline_setup("fcc_voronoi1")          # FCC + its Voronoi generators x 2
+    with pytest.raises(InterpError):
+        Interpolator(np.asarray(lat.L), xi, dims)
+    with pytest.raises(InterpError):
+        Interpolator.named("no_such_spline", dims)
 
 
 def test_eval_host_matches_device_path():

@@ -6,7 +6,7 @@ import pytest
 import oracle
 from synth import LATTICES, SPLINES, make_rng, ray_points, ray_setup
 
-from _gpu_common import VALUE_TOL, grad_bound, require_cuda
+from _gpu_common import VALUE_TOL, OracleSpline, grad_bound, make_interpolator, require_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -19,14 +19,15 @@ def _geometry(setup, W, H, steps):
     return origin, du, dv
 
 
-@pytest.mark.parametrize("name,grad", [("bcc_quintic", True), ("bcc_quintic", False), ("cc_7dir", True)])
+@pytest.mark.parametrize("name,grad", [("bcc_quintic", True), ("bcc_quintic", False), ("cc_7dir", True),
+                                       ("bcc_voronoi2", True), ("fcc_voronoi1", False)])
 def test_rays_match_oracle(name, grad):
     torch = require_cuda()
-    from paper_2102_08514_b300.binding import Interpolator, interp_eval_rays, make_rays
+    from paper_2102_08514_b300.binding import interp_eval_rays, make_rays
     sp = SPLINES[name]
     lat = LATTICES[sp.lattice]
     dims = (14, 14, 14)
-    itp = Interpolator(np.asarray(lat.L), np.asarray(sp.xi), dims, "f32")
+    itp = make_interpolator(name, dims)
     c = make_rng(61, 1).uniform(-1, 1, itp.shape).astype(np.float32)
     itp.set_coeffs(torch.from_numpy(c).cuda())
     W, H, steps = 37, 21, 48                 # ragged against the 16 x 8 pixel blocks
@@ -46,11 +47,11 @@ def test_rays_match_oracle(name, grad):
     assert np.abs(pts.reshape(-1, steps, 3)[valid] - ref_pts[valid]).max() < 1e-3
     assert np.all(out.reshape(H * W, -1)[~valid] == 0.0)
     # sums against the oracle at the GPU's points, for a sample of pixels
-    o = oracle.Spline(np.asarray(sp.xi), abs(round(np.linalg.det(np.asarray(lat.L, float)))))
-    sel = make_rng(62, 0).choice(np.flatnonzero(valid), 24, replace=False)
+    o = OracleSpline(name)
+    sel = make_rng(62, 0).choice(np.flatnonzero(valid), 8 if sp.order > 1 else 24, replace=False)
     P = pts.reshape(-1, steps, 3)[sel].reshape(-1, 3).astype(np.float64)
     if grad:
-        v, g = oracle.eval_sum(o, lat.D, lat.cosets, c.astype(np.float64), P, grad=True)
+        v, g = o.eval_sum(lat.D, lat.cosets, c, P, grad=True)
         G = grad_bound(name, P[::97])
         ref = np.concatenate([v.reshape(-1, steps).sum(1)[:, None], g.reshape(-1, steps, 3).sum(1)], axis=1)
         got = out.reshape(H * W, 4)[sel]
@@ -58,10 +59,36 @@ def test_rays_match_oracle(name, grad):
         assert np.abs(got[:, 0] - ref[:, 0]).max() <= steps * VALUE_TOL * cm
         assert np.abs(got[:, 1:] - ref[:, 1:]).max() <= steps * VALUE_TOL * cm * G
     else:
-        v = oracle.eval_sum(o, lat.D, lat.cosets, c.astype(np.float64), P)
+        v = o.eval_sum(lat.D, lat.cosets, c, P)
         ref = v.reshape(-1, steps).sum(1)
         got = out.reshape(H * W)[sel]
         assert np.abs(got - ref).max() <= steps * VALUE_TOL * np.abs(c).max()
+
+
+@pytest.mark.parametrize("name,steps", [("bcc_voronoi1", 48), ("fcc_voronoi2", 48), ("bcc_voronoi2", 700)])
+def test_binned_rays_equal_plain_rays(name, steps, monkeypatch):
+    # multi-piece splines march rays with the piece-binned kernel (whole rays per tile, sums in
+    # step and coset order); INTERP_B300_BINNED=0 selects the plain kernel: identical sums
+    torch = require_cuda()
+    from paper_2102_08514_b300.binding import interp_eval_rays, make_rays
+    dims = (12, 13, 11)
+    itp = make_interpolator(name, dims)
+    itp.set_coeffs(torch.from_numpy(make_rng(63, 1).uniform(-1, 1, itp.shape).astype(np.float32)).cuda())
+    W, H = 29, 17
+    setup = ray_setup(name, dims, W, H, steps)
+    origin, du, dv = _geometry(setup, W, H, steps)
+    rays = make_rays(origin, du, dv, setup["d"], setup["lo"], setup["hi"], W, H, steps)
+    res = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("INTERP_B300_BINNED", flag)
+        for grad in (False, True):
+            out = torch.full((W * H * (4 if grad else 1),), 7.0, device="cuda")
+            pts = torch.empty(W * H * steps * 3, device="cuda")
+            interp_eval_rays(itp.handle, rays, out, with_grad=grad, pts_out=pts)
+            res.append((out, pts))
+    for (a, pa), (b, pb) in zip(res[:2], res[2:]):
+        assert torch.equal(a, b)
+        assert torch.equal(torch.nan_to_num(pa, nan=7.0), torch.nan_to_num(pb, nan=7.0))
 
 
 def test_rays_reject_4d_and_half_storage():
