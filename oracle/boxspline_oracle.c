@@ -529,15 +529,14 @@ static int for_each_site(const orc_spline *sp, orc_memo *mm, const orc_layout *l
             for (int a = 0; a < s; ++a)
                 Z[a] = X[a] - ((i128)(ly->D * (int64_t)i[a] + ly->lk[k * s + a]) << ORC_F);
             double phi, g[ORC_MAXS] = {0, 0, 0, 0};
-            int e = phi_fixed(sp, mm, Z, &phi, NULL);
+            /* the gradient is the limit along x + eps*v like every decision, also where phi = 0
+             * exactly: on the boundary of the support a continuous but not C^1 phi has a nonzero
+             * one-sided gradient pointing into the support */
+            int e = phi_fixed(sp, mm, Z, &phi, want_grad ? g : NULL);
             if (e) return e;
-            /* where phi = 0 exactly its gradient is taken as 0 (true off the support boundary) */
-            if (phi != 0.0 && want_grad) {
-                e = phi_fixed(sp, mm, Z, &phi, g);
-                if (e) return e;
-            }
-            if (phi != 0.0)
-                fn(ctx, k, (int64_t)k * sitesz + lin_index(i, ly->dims, s), phi, g);
+            int nz = phi != 0.0;
+            for (int a = 0; a < s; ++a) nz |= g[a] != 0.0;
+            if (nz) fn(ctx, k, (int64_t)k * sitesz + lin_index(i, ly->dims, s), phi, g);
             int a = s - 1;
             while (a >= 0) {
                 if (++i[a] <= hi[a]) break;

@@ -156,3 +156,25 @@ def test_gradient_matches_finite_differences():
         e[a] = h
         fd = (v.phi(x + e) - v.phi(x - e)) / (2 * h)
         assert np.abs(fd - g[:, a]).max() < 1e-6
+
+
+@pytest.mark.parametrize("name", ["bcc_voronoi1", "fcc_voronoi1", "cc_voronoi1", "bcc_linear"])
+def test_gradient_at_exact_ties_is_the_one_sided_limit(name):
+    # every decision, the gradient included, is the limit along x + eps v with the oracle's
+    # v = (1, 2^-12, 2^-24) (direction); at points exactly on mesh planes and support boundaries
+    # of a continuous, not C^1 spline the gradient must equal that limit
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from _gpu_common import OracleSpline
+    sp = SPLINES[name]
+    lat = LATTICES[sp.lattice]
+    o = OracleSpline(name)
+    c = np.random.default_rng(21).uniform(-1, 1, (len(lat.cosets), 9, 9, 9))
+    rng = np.random.default_rng(22)
+    x = np.round(rng.uniform(5, 12, (40, 3)) * 2) / 2              # integers and halves: ties
+    x[::2, 2] += np.round(rng.uniform(0, 1, 20) * 2 ** 10) / 2 ** 10
+    v = np.array([1.0, 2.0 ** -12, 2.0 ** -24])
+    f0, g0 = o.eval_sum(lat.D, lat.cosets, c, x, grad=True)
+    f1, g1 = o.eval_sum(lat.D, lat.cosets, c, x + 2.0 ** -36 * v, grad=True)
+    assert np.abs(f0 - f1).max() < 1e-9
+    assert np.abs(g0 - g1).max() < 1e-9
