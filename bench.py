@@ -391,6 +391,17 @@ def run_ours(args):
         form_ms.update(time_rays(torch, itp, wl, fsteps, fw, stream, barrier))
     if wl.name == "fcc_6dir_128" and args.storage == "f32":
         form_ms["fit_step"] = time_fit_step(torch, itp, wl, pts, pts_h, fsteps, fw, stream, barrier)
+    prefilter_gbs = None
+    if sp.lattice == "d4":
+        # Sec. 5.2's prefilter over the whole coefficient set (samples -> padded storage); its
+        # algorithmic traffic is one 4-byte read and one write per site (the 25 taps hit cache)
+        from paper_2102_08514_b300.binding import d4_quasi_interpolation_filter
+        taps, wts = d4_quasi_interpolation_filter()
+        samples = torch.from_numpy(c).cuda()
+        _, per_p = time_steps(torch, lambda: itp.prefilter(samples, taps, wts), fsteps, fw, stream, barrier)
+        form_ms["prefilter"] = statistics.mean(per_p)
+        itp.set_coeffs(samples)
+        prefilter_gbs = itp.info.coeff_count * 8 / (form_ms["prefilter"] * 1e-3) / 1e9
 
     # e2e: points from pinned host memory, the step, results back to pinned host memory
     pts_pin = torch.from_numpy(pts_h).pin_memory()
@@ -459,6 +470,9 @@ def run_ours(args):
         "forms": {k: {"evals_per_s": (RAY_EVALS[0] if k.startswith("rays") else n) / (v * 1e-3), "ms": v}
                   for k, v in form_ms.items()},
     }
+    if prefilter_gbs is not None:
+        line["forms"]["prefilter"] = {"ms": form_ms["prefilter"], "sites": int(itp.info.coeff_count),
+                                      "gb_per_s": prefilter_gbs, "hbm_frac_of_measured": prefilter_gbs / peaks()[0]["hbm_gbs"]}
     line["forms"]["value"]["tflops"] = 2.0 * info.fma_value_per_query * n / (form_ms["value"] * 1e-3) / 1e12
     line["forms"]["value_grad"]["tflops"] = 2.0 * info.fma_grad_per_query * n / (form_ms["value_grad"] * 1e-3) / 1e12
     if args.workload != WORKLOAD or args.storage != "f32" or form != DEFAULT_FORM[WORKLOAD] or args.spline:

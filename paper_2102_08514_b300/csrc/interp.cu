@@ -87,44 +87,120 @@ __global__ void k_pad_copy(const ST *__restrict__ src, CT *__restrict__ dst, int
 }
 
 // the taps of a lattice filter resolved per output coset: tap t of output coset k reads the
-// samples of coset src[k][t] at index i + shift[k][t] (passed by value as a kernel parameter)
+// samples of coset src[k][t] at index i + shift[k][t], i.e. at linear offset delta[k][t] from
+// the output's own sample (passed by value as a kernel parameter)
 constexpr int kMaxTaps = 64;
 struct PrefilterTaps {
     int ntaps;
+    int reach;                       // largest |shift| over taps and axes
     float w[kMaxTaps];
+    int delta[8][kMaxTaps];
+    unsigned char neg[8][kMaxTaps];  // axes on which the tap's index shift is -1 (reach 1)
+    unsigned char pos[8][kMaxTaps];  // axes on which it is +1
     signed char src[8][kMaxTaps];
     signed char shift[8][kMaxTaps][4];
 };
 
 // c_k[i] = sum_t w_t f_src[i + shift] over the taps (samples taken as zero outside the arrays),
-// rounded to the storage type and written to the interior of the padded, bricked arrays.  One
-// thread per output site in sample order (row-major), so the reads of every tap are coalesced.
+// rounded to the storage type and written to the interior of the padded, bricked arrays.
+// A thread computes the outputs of all M cosets at PF_RUN consecutive sites along the last axis,
+// so the taps of every coset read the same neighbourhood of every coset array while it is in
+// cache (each input is fetched from DRAM about once) and each tap's address and bounds test serve
+// PF_RUN loads.  A CTA covers whole rows (all axes but the last fixed).  Bounds are tested without
+// branches (face masks against the taps' sign masks) for filters that reach one index step (all
+// filters on nearest neighbours), per tap and axis for longer ones.
+constexpr int PF_RUN = 4;
+
 template <class CT>
-__global__ void k_prefilter(const float *__restrict__ f, CT *__restrict__ dst, int64_t total, ibl::Layout L,
-                            PrefilterTaps tp)
+__global__ void __launch_bounds__(256) k_prefilter(const float *__restrict__ f, CT *__restrict__ dst, ibl::Layout L,
+                                                   int lw, int chunks, int nrows, int M, int cstride, PrefilterTaps tp)
 {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        int idx[4] = {0, 0, 0, 0};
-        int64_t r = e;
-        for (int a = L.s - 1; a >= 0; --a) {
-            idx[a] = (int)(r % L.n[a]);
-            r /= L.n[a];
+    const int s = L.s, nl = L.n[s - 1];
+    int row, i0;                                     // the thread's first site on the row
+    if (chunks == 1) {                               // several rows of 2^lw threads per CTA
+        row = blockIdx.x * (blockDim.x >> lw) + (threadIdx.x >> lw);
+        i0 = (threadIdx.x & ((1 << lw) - 1)) * PF_RUN;
+    } else {                                         // rows longer than a CTA: `chunks` CTAs per row
+        row = blockIdx.x / chunks;
+        i0 = ((blockIdx.x % chunks) * blockDim.x + threadIdx.x) * PF_RUN;
+    }
+    if (row >= nrows || i0 >= nl) return;
+    int idx[4] = {0, 0, 0, 0};
+    int r = row;
+    for (int a = s - 2; a >= 0; --a) {
+        idx[a] = r % L.n[a];
+        r /= L.n[a];
+    }
+    const int la = s - 1;
+    const int e0 = row * nl + i0;                    // linear index of the first site within a coset
+    int p[4];
+    for (int a = 0; a < 4; ++a) p[a] = idx[a] + L.pad;
+    if (tp.reach <= 1) {
+        // face masks of the axes but the last (shared by the run) and per site of the last axis
+        unsigned lo = 0, hi = 0;
+        for (int a = 0; a < la; ++a) {
+            lo |= (idx[a] == 0 ? 1u : 0u) << a;
+            hi |= (idx[a] == L.n[a] - 1 ? 1u : 0u) << a;
         }
-        const int k = (int)r;
-        float acc = 0.0f;
-        for (int t = 0; t < tp.ntaps; ++t) {
-            int64_t off = tp.src[k][t];
-            bool in = true;
-            for (int a = 0; a < L.s; ++a) {
-                const int j = idx[a] + tp.shift[k][t][a];
-                in &= (unsigned)j < (unsigned)L.n[a];
-                off = off * L.n[a] + j;
+        unsigned lo_u[PF_RUN], hi_u[PF_RUN];
+        bool live[PF_RUN];
+#pragma unroll
+        for (int u = 0; u < PF_RUN; ++u) {
+            const int il = i0 + u;
+            live[u] = il < nl;
+            lo_u[u] = lo | ((il == 0 ? 1u : 0u) << la);
+            hi_u[u] = hi | ((il == nl - 1 ? 1u : 0u) << la);
+        }
+#pragma unroll 1
+        for (int k = 0; k < M; ++k) {
+            const float *fk = f + k * cstride + e0;
+            float acc[PF_RUN];
+#pragma unroll
+            for (int u = 0; u < PF_RUN; ++u) acc[u] = 0.0f;
+#pragma unroll 2
+            for (int t = 0; t < tp.ntaps; ++t) {
+                const unsigned ng = tp.neg[k][t], ps = tp.pos[k][t];
+                const int d = tp.delta[k][t];
+                const float w = tp.w[t];
+                float v[PF_RUN];
+#pragma unroll
+                for (int u = 0; u < PF_RUN; ++u) {
+                    // a tap outside the arrays (or a site past the row) reads the run's first
+                    // sample, always in bounds, and contributes 0
+                    const bool in = live[u] && !((ng & lo_u[u]) | (ps & hi_u[u]));
+                    const float x = __ldg(fk + (in ? d + u : 0));
+                    v[u] = in ? x : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < PF_RUN; ++u) acc[u] = fmaf(w, v[u], acc[u]);
             }
-            if (in) acc = fmaf(tp.w[t], __ldg(f + off), acc);
+#pragma unroll
+            for (int u = 0; u < PF_RUN; ++u) {
+                if (!live[u]) break;
+                p[la] = i0 + u + L.pad;
+                dst[ibl::elem_offset(L, k, p)] = convert_to<float, CT>(acc[u]);
+            }
         }
-        int p[4];
-        for (int a = 0; a < 4; ++a) p[a] = idx[a] + L.pad;
-        dst[ibl::elem_offset(L, k, p)] = convert_to<float, CT>(acc);
+        return;
+    }
+    // longer filters: explicit bounds per tap and axis
+    for (int u = 0; u < PF_RUN && i0 + u < nl; ++u) {
+        idx[la] = i0 + u;
+        p[la] = idx[la] + L.pad;
+#pragma unroll 1
+        for (int k = 0; k < M; ++k) {
+            const int e = k * cstride + e0 + u;
+            float acc = 0.0f;
+            for (int t = 0; t < tp.ntaps; ++t) {
+                bool in = true;
+                for (int a = 0; a < s; ++a) {
+                    const int j = idx[a] + tp.shift[k][t][a];
+                    in &= (unsigned)j < (unsigned)L.n[a];
+                }
+                if (in) acc = fmaf(tp.w[t], __ldg(f + e + tp.delta[k][t]), acc);
+            }
+            dst[ibl::elem_offset(L, k, p)] = convert_to<float, CT>(acc);
+        }
     }
 }
 
@@ -487,18 +563,46 @@ interp_status interp_prefilter(interp_t *h, const float *samples, int ntaps, con
                 tp.shift[k][t][a] = (signed char)((o.cosets[k * s + a] + taps[t * s + a] - o.cosets[kk * s + a]) / D);
         }
     }
+    // linear offsets of the taps in the sample array, and the reach of the filter
+    int64_t stride[4] = {0, 0, 0, 0}, coset_stride = 1;
+    for (int a = s - 1; a >= 0; --a) {
+        stride[a] = coset_stride;
+        coset_stride *= h->dims[a];
+    }
+    for (int k = 0; k < M; ++k)
+        for (int t = 0; t < ntaps; ++t) {
+            int64_t d = (int64_t)(tp.src[k][t] - k) * coset_stride;
+            for (int a = 0; a < s; ++a) {
+                d += tp.shift[k][t][a] * stride[a];
+                tp.reach = std::max(tp.reach, (int)std::abs(tp.shift[k][t][a]));
+                if (tp.shift[k][t][a] < 0) tp.neg[k][t] |= (unsigned char)(1u << a);
+                if (tp.shift[k][t][a] > 0) tp.pos[k][t] |= (unsigned char)(1u << a);
+            }
+            tp.delta[k][t] = (int)d;
+        }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const unsigned grid = (unsigned)std::min<int64_t>((h->coeff_count + 255) / 256, 148 * 32);
+    const int nl = h->dims[s - 1];
+    const int runs = (nl + PF_RUN - 1) / PF_RUN;     // threads per row
+    int lw = 0;
+    while ((1 << lw) < runs && lw < 8) ++lw;
+    const int chunks = (runs + 255) / 256;
+    const int nrows = (int)(h->coeff_count / M / nl);
+    const int rows_per_cta = chunks == 1 ? 256 >> lw : 1;
+    const unsigned grid = chunks == 1 ? (unsigned)((nrows + rows_per_cta - 1) / rows_per_cta)
+                                      : (unsigned)((int64_t)nrows * chunks);
+    const unsigned threads = chunks == 1 ? (unsigned)(rows_per_cta << lw) : 256u;
     switch (h->storage) {
     case INTERP_F32:
-        k_prefilter<float><<<grid, 256, 0, st>>>(samples, static_cast<float *>(h->coeffs), h->coeff_count, h->lay, tp);
+        k_prefilter<float><<<grid, threads, 0, st>>>(samples, static_cast<float *>(h->coeffs), h->lay, lw, chunks,
+                                                     nrows, M, (int)coset_stride, tp);
         break;
     case INTERP_F16:
-        k_prefilter<__half><<<grid, 256, 0, st>>>(samples, static_cast<__half *>(h->coeffs), h->coeff_count, h->lay, tp);
+        k_prefilter<__half><<<grid, threads, 0, st>>>(samples, static_cast<__half *>(h->coeffs), h->lay, lw, chunks,
+                                                      nrows, M, (int)coset_stride, tp);
         break;
     default:
-        k_prefilter<__nv_bfloat16><<<grid, 256, 0, st>>>(samples, static_cast<__nv_bfloat16 *>(h->coeffs),
-                                                         h->coeff_count, h->lay, tp);
+        k_prefilter<__nv_bfloat16><<<grid, threads, 0, st>>>(samples, static_cast<__nv_bfloat16 *>(h->coeffs), h->lay,
+                                                             lw, chunks, nrows, M, (int)coset_stride, tp);
         break;
     }
     return cuda_status(cudaPeekAtLastError());

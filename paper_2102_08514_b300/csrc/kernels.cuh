@@ -210,25 +210,36 @@ struct Slot {
     int wt;   // within-brick weight of that axis
 };
 
+// Ties are decided as for the point x + eps v, eps -> 0+, with the fixed world direction
+// v = (1, 2^-12, 2^-24, 2^-36) (the direction the oracle uses), so that every coset takes the same
+// side of a plane through x: values are continuous there, but a C^0 spline's gradient is not, and
+// cosets deciding independently would sum one-sided gradients of different sides.
+// |y_a + eps v_a| = |y_a| + eps sg_a v_a: on |y_a| = |y_b| the slot with the larger sg v comes
+// first; sg (4 - ax) orders sg v the same way (v decreases with the axis).
+// Only a spline that is not C^1 needs the tie rule in the sort (TIE): for a C^1 spline either
+// order gives the same value and gradient on a fold wall.
+template <bool TIE>
 __device__ __forceinline__ void cswap(Slot &a, Slot &b)
 {
-    // descending order; ties keep the current order (either order is valid on a chamber wall)
-    const bool sw = a.y < b.y;
+    // descending order of |y| (and of sg v[ax] on ties if TIE)
+    bool sw = a.y < b.y;
+    if constexpr (TIE) sw |= a.y == b.y && a.sg * (4 - a.ax) < b.sg * (4 - b.ax);
     const Slot lo = sw ? a : b;
     const Slot hi = sw ? b : a;
     a = hi;
     b = lo;
 }
 
-template <int S>
+template <int S, bool TIE>
 __device__ __forceinline__ void sort_desc(Slot (&sl)[S])
 {
     if constexpr (S == 2) {
-        cswap(sl[0], sl[1]);
+        cswap<TIE>(sl[0], sl[1]);
     } else if constexpr (S == 3) {
-        cswap(sl[0], sl[1]); cswap(sl[1], sl[2]); cswap(sl[0], sl[1]);
+        cswap<TIE>(sl[0], sl[1]); cswap<TIE>(sl[1], sl[2]); cswap<TIE>(sl[0], sl[1]);
     } else if constexpr (S == 4) {
-        cswap(sl[0], sl[1]); cswap(sl[2], sl[3]); cswap(sl[0], sl[2]); cswap(sl[1], sl[3]); cswap(sl[1], sl[2]);
+        cswap<TIE>(sl[0], sl[1]); cswap<TIE>(sl[2], sl[3]); cswap<TIE>(sl[0], sl[2]); cswap<TIE>(sl[1], sl[3]);
+        cswap<TIE>(sl[1], sl[2]);
     }
 }
 
@@ -262,6 +273,28 @@ __device__ __forceinline__ int slot_term(const Slot &sl, int o)
 {
     const int v = sl.p + sl.sg * o;
     return (v >> sl.lb) * sl.bs + (v & ((1 << sl.lb) - 1)) * sl.wt;
+}
+
+// side of plane I for the folded offset in the slots, exactly: the sum in FP64 with the terms in
+// descending order (y' sorted) is exact or keeps its sign; exactly on the plane, the side of
+// y' + eps v' with v' the folded image of the world direction v (the term of the smallest
+// original axis decides, v being lexicographic)
+template <class SP, int I, int S>
+__device__ __forceinline__ bool plane_side_exact(const Slot (&sl)[S])
+{
+    double d = -(double)SP::PLANE_E[I];
+    int best_ax = 99, sgn = 1;
+    sfor<S>([&](auto A) {
+        constexpr int p = SP::PLANE_P[I][decltype(A)::value];
+        if constexpr (p != 0) {
+            d = fma((double)p, (double)sl[A].y, d);
+            if (sl[A].ax < best_ax) {
+                best_ax = sl[A].ax;
+                sgn = p * sl[A].sg;
+            }
+        }
+    });
+    return d != 0.0 ? d > 0.0 : sgn > 0;
 }
 
 // steps 1-3 for coset K of spline SP (K < 0: the run-time coset index kr)
@@ -299,7 +332,7 @@ __device__ __forceinline__ Fold<SP::S> fold_coset(const float (&x)[SP::S], const
         sl.bs = v.L.bstride[a];
         sl.wt = v.L.wt[a];
     });
-    sort_desc<S>(f.sl);
+    sort_desc<S, (SP::SMOOTH < 1)>(f.sl);
     sfor<S>([&](auto A) { f.t[A] = f.sl[A].y; });
     int j = 0;
     if constexpr (SP::K > 1) {
@@ -312,7 +345,11 @@ __device__ __forceinline__ Fold<SP::S> fold_coset(const float (&x)[SP::S], const
                 constexpr int p = SP::PLANE_P[i][decltype(A)::value];
                 if constexpr (p != 0) acc = fmaf((float)p, f.t[A], acc);
             });
-            q |= (acc >= 0.0f ? 1u : 0u) << i;
+            // the FP32 value is within 2^-19 of p . y' - e (|p_a| = 1, y' <= 1, |e| <= 5/2 for
+            // every built-in table); near zero decide exactly
+            bool ge = acc >= 0.0f;
+            if (fabsf(acc) <= 0x1p-17f) ge = plane_side_exact<SP, i>(f.sl);
+            q |= (ge ? 1u : 0u) << i;
         });
         if constexpr (SP::R > 64) {
             j = (int)SP::sigma_at(q);                   // byte table in device memory

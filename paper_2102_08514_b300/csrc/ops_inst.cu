@@ -58,13 +58,23 @@ template <class CT, int MODE, int T, int NT>
     return cudaPeekAtLastError();
 }
 
-// queries per tile of the piece-binned kernels: 1024, or fewer when the tile's (query, coset)
-// items would not fit shared memory (many cosets, e.g. the 8 of D4)
+// queries per tile of the piece-binned kernels.  Each tile re-fetches the code of every piece it
+// meets, so splines with large pieces (>= 400 nonzeros, instruction-fetch bound) take 2048-query
+// tiles; the others 1024.  The tile's shared memory stays within 170 KB: beyond that the L1 data
+// cache left for the coefficient gathers is too small (measured: BCC V_2 value+grad 12.2 -> 6.8 ms
+// with 2048-query tiles (168 KB); BCC V_1 (75 nonzeros) 0.82 -> 1.01 ms; D4* value+grad
+// 4.2 -> 7.1 ms at 200 KB).  8-coset D4 drops to 512 / 256.
+constexpr size_t kBinSmemBudget = 170 * 1024;
+
 template <int MODE>
 constexpr int bin_tile()
 {
-    return ib::binned_smem_bytes<SP, MODE, 1024>() <= kMaxSmem ? 1024
-           : ib::binned_smem_bytes<SP, MODE, 512>() <= kMaxSmem ? 512 : 256;
+    if constexpr (SP::NNZMAX >= 400 && ib::binned_smem_bytes<SP, MODE, 2048>() <= kBinSmemBudget &&
+                  SP::M * 2048 <= 65535)
+        return 2048;
+    else
+        return ib::binned_smem_bytes<SP, MODE, 1024>() <= kBinSmemBudget ? 1024
+               : ib::binned_smem_bytes<SP, MODE, 512>() <= kBinSmemBudget ? 512 : 256;
 }
 
 template <class CT, int MODE>

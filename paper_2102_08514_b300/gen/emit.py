@@ -116,6 +116,7 @@ def emit_struct(T, half_storage: bool = True) -> tuple[str, dict]:
     L.append(f"    static constexpr int K = {K}, Q = {Q}, R = {T.r}, DEG = {T.degree}, NMON = {nmon}, HALO = {T.halo};")
     L.append(f"    static constexpr int NSMAX = {nsmax}, NNZMAX = {nnzmax}, FOLD = {T.fold};")
     L.append(f"    static constexpr int KIND = {T.kind};  // 0: box spline M_XI; n: Voronoi spline V_n, XI = 2 G")
+    L.append(f"    static constexpr int SMOOTH = {T.smooth};  // phi is in C^SMOOTH")
     L.append(f"    static constexpr bool HALF_STORAGE = {'true' if half_storage else 'false'};  // FP16/BF16 kernels built")
     L.append(f"    static constexpr int XI[S][NXI] = {_arr([_arr(r) for r in T.xi])};")
     L.append(f"    static constexpr int LMAT[S][S] = {_arr([_arr(r) for r in T.L])};")
@@ -170,7 +171,7 @@ def emit_struct(T, half_storage: bool = True) -> tuple[str, dict]:
     L.append(f"    static constexpr double FMA_VALUE = {fma_value!r}, FMA_GRAD = {fma_grad!r}, LOOKUPS = {lookups!r};")
     L.append("};")
 
-    meta = dict(name=T.name, kind=T.kind, s=s, L=T.L, xi=T.xi, det_l=T.det_l, D=T.D, cosets=T.cosets, fold=T.fold,
+    meta = dict(name=T.name, kind=T.kind, smooth=T.smooth, s=s, L=T.L, xi=T.xi, det_l=T.det_l, D=T.D, cosets=T.cosets, fold=T.fold,
                 degree=T.degree, n_monomials=nmon, halo=T.halo, r=T.r, sigma=T.sigma,
                 planes=[[list(p), str(e)] for p, e in T.planes],
                 r_sec42=sec42_compression([pc.code for pc in T.pieces], len(T.planes)),
@@ -211,6 +212,10 @@ def main(argv=None):
         T = analyse_entry(name)
         if len(T.pieces) > MAX_PIECES or len(T.planes) > MAX_Q:
             raise ValueError(f"{name}: {len(T.pieces)} pieces / {len(T.planes)} planes exceed the kernels' sigma table")
+        # the kernels' FP32 plane test is within 2^-19 of exact for |p_a| <= 1, |e| <= 4 (they
+        # recompute exactly below 2^-17)
+        if any(abs(a) > 1 for p_, _ in T.planes for a in p_) or any(abs(e) > 4 for _, e in T.planes):
+            raise ValueError(f"{name}: plane coefficients outside the kernels' exact-test bound")
         text, meta = emit_struct(T, half_storage=name in HALF_STORAGE)
         structs.append(text)
         metas[name] = meta

@@ -322,6 +322,7 @@ class SplineTables:
     halo: int             # max |g_a| over all stencil sites (grid units)
     lookups: int = 0      # coefficient reads per query (all cosets)
     kind: int = 0         # 0: box spline M_Xi; n >= 1: Voronoi spline V_n (xi records 2 G)
+    smooth: int = 0       # phi is in C^smooth
 
 
 @dataclass(frozen=True)
@@ -539,7 +540,26 @@ def analyse_terms(name, L, terms, fold, xi_record, kind, anchor_den=64, verbose=
     halo = max((abs(g[a]) for pc in pieces for g in pc.sites for a in range(s)), default=0)
     lookups = max(len(pc.sites) for pc in pieces) * len(cosets)
     return SplineTables(name, s, [list(r_) for r_ in L], xi_record, det_l, D, cosets,
-                        fold, degree, planes, r, sigma, pieces, halo, lookups, kind)
+                        fold, degree, planes, r, sigma, pieces, halo, lookups, kind, smoothness(terms, s))
+
+
+def smoothness(terms, s):
+    """Continuity order k (phi in C^k) of a sum of box splines, the smallest over the terms: a box
+    spline M_C is in C^(m-2), m the fewest columns whose removal leaves C not spanning R^s (the
+    columns off some hyperplane spanned by columns of C) -- Sec. 3's smoothness of box splines."""
+    best = None
+    for t in terms:
+        dirs = sorted({_canon_dir(c) for c in t.cols})
+        m = None
+        for sub in itertools.combinations(dirs, s - 1):
+            p = hyperplane_normal(list(sub), s)
+            if p is None:
+                continue
+            off = sum(1 for c in t.cols if sum(p[a] * c[a] for a in range(s)) != 0)
+            m = off if m is None else min(m, off)
+        k = m - 2
+        best = k if best is None else min(best, k)
+    return best
 
 
 def sec42_compression(codes, Q):

@@ -124,6 +124,37 @@ def test_adjoint_parity(name):
     assert np.all(err <= 4e-6 * bound + 1e-7), (err.max(), bound.max())
 
 
+@pytest.mark.parametrize("name", ["bcc_linear", "cc_linear_rd", "cc_voronoi1", "bcc_voronoi1", "fcc_voronoi1"])
+def test_gradient_at_exact_ties(name):
+    # continuous, not C^1 splines: at points exactly on mesh planes (integer, half and quarter
+    # coordinates, and sums of them) the gradient is the one-sided limit along the fixed world
+    # direction v = (1, 2^-12, 2^-24), on the GPU (every coset and fold decision) as in the oracle
+    n_axis = SMALL[name][0]
+    sp, lat, xi, detl = spline_setup(name)
+    dims = (n_axis,) * 3
+    torch, itp = _interp(name, dims)
+    c = _coeffs(name, dims, 24)
+    itp.set_coeffs(torch.from_numpy(c).cuda())
+    lo, hi = interior_box(name, dims)
+    rng = make_rng(25, 0)
+    pts = (np.round(rng.uniform(lo, hi, (1500, 3)) * 4) / 4).astype(np.float32)
+    pts[::3, 1] = (np.round(rng.uniform(lo[1], hi[1], 500) * 2 ** 12) / 2 ** 12).astype(np.float32)
+    pts[1::3, 0] = (np.floor(pts[1::3, 1]) + 0.5 - (pts[1::3, 1] - np.floor(pts[1::3, 1]))).astype(np.float32)
+    for flag in ("1", "0") if SPLINES[name].order else ("0",):
+        import os
+        os.environ["INTERP_B300_BINNED"] = flag
+        try:
+            val, grad = itp.eval_grad(torch.from_numpy(pts).cuda())
+        finally:
+            os.environ.pop("INTERP_B300_BINNED")
+        ref_v, ref_g = OracleSpline(name).eval_sum(lat.D, lat.cosets, c, pts, grad=True)
+        cmax = np.abs(c).max()
+        G = grad_bound(name, pts[:16])
+        assert np.abs(val.cpu().numpy() - ref_v).max() <= VALUE_TOL * cmax
+        gerr = np.abs(grad.cpu().numpy() - ref_g).max()
+        assert gerr <= VALUE_TOL * cmax * G, (gerr, int(np.abs(grad.cpu().numpy() - ref_g).max(axis=1).argmax()))
+
+
 @pytest.mark.parametrize("name", ["bcc_quintic", "fcc_6dir"])
 def test_pullback_dpts(name):
     n_axis, nq = SMALL[name]
