@@ -126,20 +126,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def recorded_traffic(kernel: str):
-    """DRAM bytes per launch from the last ncu capture (profiles/traffic.txt), or None when the
-    library sources changed since that capture."""
+def recorded_capture(kernel: str):
+    """(DRAM bytes per launch, binding-resource fraction) from the last ncu capture of the kernel
+    (profiles/traffic.txt), or (None, None) when the library sources changed since that capture.
+    The binding resource of the random-query gather is the L1 -> L2 miss-request path
+    (l1tex__m_l1tex2xbar_req_cycles_active, fraction of its peak)."""
     from paper_2102_08514_b300 import build as b
     digest = b.source_digest()[:16]
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.txt")) as f:
             for line in f:
                 parts = line.split()
-                if len(parts) == 3 and parts[0] == kernel and parts[1] == digest:
-                    return int(parts[2])
+                if len(parts) >= 3 and parts[0] == kernel and parts[1] == digest:
+                    return int(parts[2]), (float(parts[3]) if len(parts) > 3 else None)
     except OSError:
         pass
-    return None
+    return None, None
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -439,7 +441,7 @@ def run_ours(args):
     achieved = flops_per_launch / (kern_ms * 1e-3) / 1e12
     peak = fp32_peak_tflops()
     kname = f"k_eval<{wl.spline},{args.storage},{form}>" if form != "adjoint" else f"k_adjoint<{wl.spline}>"
-    traffic = recorded_traffic(kname)
+    traffic, l1l2_frac = recorded_capture(kname)
     line = {
         "metric": METRIC,
         "value": value,
@@ -466,7 +468,12 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": kname,
                      "flops_per_query": 2.0 * fma,
-                     "peak_note": "FP32 FMA peak derived: 148 SMs x 128 lanes x 2 FLOP x 2032 MHz (of derived)"},
+                     "peak_note": "FP32 FMA peak derived: 148 SMs x 128 lanes x 2 FLOP x 2032 MHz (of derived)",
+                     # random queries are bound by the gather's L1 -> L2 miss requests, not the
+                     # FP32 pipe: that path's fraction of its peak, from the kernel's ncu capture
+                     "binding_resource": {"name": "L1 -> L2 miss requests (l1tex__m_l1tex2xbar_req_cycles_active)",
+                                          "frac_of_peak": l1l2_frac,
+                                          "source": "ncu capture, profiles/k_eval_bcc_quintic_value_grad.md"}},
         "forms": {k: {"evals_per_s": (RAY_EVALS[0] if k.startswith("rays") else n) / (v * 1e-3), "ms": v}
                   for k, v in form_ms.items()},
     }
@@ -475,6 +482,14 @@ def run_ours(args):
                                       "gb_per_s": prefilter_gbs, "hbm_frac_of_measured": prefilter_gbs / peaks()[0]["hbm_gbs"]}
     line["forms"]["value"]["tflops"] = 2.0 * info.fma_value_per_query * n / (form_ms["value"] * 1e-3) / 1e12
     line["forms"]["value_grad"]["tflops"] = 2.0 * info.fma_grad_per_query * n / (form_ms["value_grad"] * 1e-3) / 1e12
+    for k in ("rays_value", "rays_value_grad"):
+        # ray-coherent samples hit L1 / L2, so the FP32 pipe is their binding roofline
+        if k in form_ms:
+            fma_s = info.fma_value_per_query if k == "rays_value" else info.fma_grad_per_query
+            line["forms"][k]["tflops"] = 2.0 * fma_s * RAY_EVALS[0] / (form_ms[k] * 1e-3) / 1e12
+    for k in ("value", "value_grad", "rays_value", "rays_value_grad"):
+        if k in line["forms"] and "tflops" in line["forms"][k]:
+            line["forms"][k]["frac_of_fp32_peak"] = line["forms"][k]["tflops"] / peak
     if args.workload != WORKLOAD or args.storage != "f32" or form != DEFAULT_FORM[WORKLOAD] or args.spline:
         line["metric"] = f"evals/s ({form}, {args.storage} storage)"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -83,3 +83,32 @@ def test_batch_rejects_half_storage_and_bad_tiles():
     assert e.value.status == INTERP_EINVAL
     b.set_tiles({"bcc_quintic": 256})
     assert b.tiles() == {"bcc_quintic": 256}
+
+
+def test_batch_with_handles_outside_the_persistent_kernel():
+    # splines outside the persistent kernel's list (many-piece or heavy 3-D splines, 4-D) run their
+    # own evaluation launch inside the same graph; a batch mixing both groups equals the
+    # per-handle path, and only the persistent kernel's splines report a tile
+    torch = require_cuda()
+    from paper_2102_08514_b300.binding import Batch
+    from _gpu_common import make_interpolator
+    names = ["bcc_voronoi1", "bcc_quintic", "cc_voronoi3", "fcc_voronoi2", "d4_8dir", "cc_7dir"]
+    items, cs = [], []
+    for v, name in enumerate(names):
+        s = len(SPLINES[name].xi)
+        dims = (6,) * 4 if s == 4 else (9, 10, 11)
+        itp = make_interpolator(name, dims)
+        c = make_rng(300 + v, 1).uniform(-1, 1, itp.shape).astype(np.float32)
+        itp.set_coeffs(torch.from_numpy(c).cuda())
+        lo, hi = interior_box(name, dims)
+        nq = 700 + 37 * v
+        pts = torch.from_numpy(uniform_points(make_rng(400 + v, 2), nq, lo, hi)).cuda()
+        items.append((itp, pts, torch.full((nq,), float("nan"), device="cuda")))
+        cs.append(c)
+    batch = Batch(items)
+    assert set(batch.tiles()) == {"bcc_quintic", "cc_7dir"}
+    batch.run()
+    torch.cuda.synchronize()
+    for (itp, pts, out), c, name in zip(items, cs, names):
+        ref = itp.eval(pts)
+        assert torch.allclose(out, ref, rtol=0, atol=VALUE_TOL * float(np.abs(c).max())), name
