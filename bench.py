@@ -132,7 +132,7 @@ def recorded_capture(kernel: str):
     The binding resource of the random-query gather is the L1 -> L2 miss-request path
     (l1tex__m_l1tex2xbar_req_cycles_active, fraction of its peak)."""
     from paper_2102_08514_b300 import build as b
-    digest = b.source_digest()[:16]
+    digest = b.kernel_digest()[:16]
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.txt")) as f:
             for line in f:
@@ -433,6 +433,29 @@ def run_ours(args):
     e2e_steps = max(3, min(args.steps, 10))
     e2e_ms, _ = time_steps(torch, e2e_step, e2e_steps, fw, stream, barrier)
     e2e_ms = max_over_ranks(e2e_ms) / e2e_steps
+    # the copy engines' bound on the same bytes: plain pinned copies of the step's sizes, each
+    # direction alone; the pipelined step overlaps the two directions and the evaluation
+    hb = torch.empty(h2d // 4, pin_memory=True)
+    hd = torch.empty(h2d // 4, device="cuda")
+    db = torch.empty(d2h // 4, pin_memory=True)
+    dd = torch.empty(d2h // 4, device="cuda")
+    h2d_ms, _ = time_steps(torch, lambda: hd.copy_(hb, non_blocking=True), 3, 2, stream, barrier)
+    d2h_ms, _ = time_steps(torch, lambda: db.copy_(dd, non_blocking=True), 3, 2, stream, barrier)
+    side = torch.cuda.Stream()
+
+    def both():
+        # the two directions at once, on two streams (as the pipelined step runs them)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            db.copy_(dd, non_blocking=True)
+        hd.copy_(hb, non_blocking=True)
+        stream.wait_stream(side)
+    both_ms, _ = time_steps(torch, both, 3, 2, stream, barrier)
+    h2d_ms /= 3
+    d2h_ms /= 3
+    both_ms /= 3
+    del hb, hd, db, dd
+    copy_bound_ms = max(h2d_ms, d2h_ms)
 
     info = itp.info
     fma = info.fma_grad_per_query if form == "value_grad" else info.fma_value_per_query
@@ -462,7 +485,12 @@ def run_ours(args):
                    "l2": f"inputs larger than L2 (points {n * s * 4 / 1e6:.0f} MB per GPU)" if n * s * 4 > 126e6
                    else f"inputs {n * s * 4 / 1e6:.0f} MB (smaller than L2)"},
         "e2e": {"value": world * n / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                "copy_bound": {"h2d_gb_per_s": h2d / (h2d_ms * 1e-3) / 1e9, "d2h_gb_per_s": d2h / (d2h_ms * 1e-3) / 1e9,
+                               "ms": copy_bound_ms, "frac": copy_bound_ms / e2e_ms,
+                               "both_directions_at_once_ms": both_ms, "frac_of_both": both_ms / e2e_ms,
+                               "note": "plain pinned copies of the step's bytes: the larger of the two directions "
+                                       "alone, and both directions at once on two streams"}},
         "gpu_launches": args.steps,
         "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

@@ -157,9 +157,9 @@ interp_status interp_eval_grad(const interp_t *h, const float *pts, int64_t npts
 /*
  * interp_eval_host -- interp_eval / interp_eval_grad for HOST buffers (not in the paper): the
  * queries are copied to the device, evaluated and copied back in chunks of 2^20 queries, with the
- * copies of one chunk overlapping the evaluation of the next (two internal streams, ordered after
- * the work already queued on `stream`; `stream` waits for all of it before later work).  For the
- * copies to overlap, pts / out / grad must be page-locked host memory (cudaHostAlloc or
+ * copies of neighbouring chunks overlapping each other and the evaluation (two internal streams,
+ * ordered after the work already queued on `stream`; `stream` waits for all of it before later
+ * work).  For the copies to overlap, pts / out / grad must be page-locked host memory (cudaHostAlloc or
  * cudaHostRegister); pageable buffers work but serialise.  grad may be NULL (value only).  The
  * handle owns the device staging buffers (allocated on first use); calls on one handle must not
  * overlap.  Returns when the work is queued; synchronise `stream` before reading out / grad.

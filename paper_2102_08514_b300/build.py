@@ -55,6 +55,17 @@ def source_digest() -> str:
     return h.hexdigest()
 
 
+def kernel_digest() -> str:
+    """Hash of what the device kernels are compiled from (kernels, layout, registry, instantiation
+    unit, generated tables, flags): unchanged while only host code of the ABI changes, so a
+    profile of a kernel stays attributable to it."""
+    h = hashlib.sha256(" ".join(NVCC_FLAGS).encode())
+    for name in ("kernels.cuh", "layout.h", "registry.h", "ops_inst.cu", os.path.join("generated", "splines.h")):
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def needs_build() -> bool:
     if not os.path.exists(OUT) or not os.path.exists(STAMP):
         return True

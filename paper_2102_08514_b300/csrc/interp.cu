@@ -364,10 +364,11 @@ struct interp {
     int device = 0;
     unsigned *sort_keys = nullptr;  // interp_sort_points bin counters
     int sort_nkeys = 0;
-    // interp_eval_host staging: two slots of (points, values, gradients) and one stream each
-    float *stage[2] = {nullptr, nullptr};
-    cudaStream_t hs[2] = {nullptr, nullptr};
-    cudaEvent_t hev[3] = {nullptr, nullptr, nullptr};
+    // interp_eval_host staging: kHostSlots slots of (points, values, gradients), one stream each
+    static constexpr int kHostSlots = 2;
+    float *stage[kHostSlots] = {};
+    cudaStream_t hs[kHostSlots] = {};
+    cudaEvent_t hev[kHostSlots + 1] = {};
 };
 
 static cudaError_t eval_launch(const interp *h, const float *pts, int64_t npts, float *out, float *grad, const float *gout,
@@ -500,7 +501,7 @@ void interp_destroy(interp_t *h)
     cudaFree(h->coeffs);
     cudaFree(h->dpad);
     cudaFree(h->sort_keys);
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < interp::kHostSlots; ++i) {
         cudaFree(h->stage[i]);
         if (h->hs[i]) cudaStreamDestroy(h->hs[i]);
     }
@@ -686,15 +687,20 @@ interp_status interp_eval_host(interp_t *h, const float *pts, int64_t npts, floa
     if (!h || npts < 0) return INTERP_EINVAL;
     if (npts == 0) return INTERP_OK;
     if (!pts || !out) return INTERP_EINVAL;
+    // chunks of 2^20 queries rotate over kHostSlots streams: a slot's upload waits only for that
+    // slot's previous download, so uploads, evaluations and downloads of neighbouring chunks
+    // overlap (measured on the BCC quintic workload: two slots of 2^20 queries 6.54 ms per 2^24
+    // queries, three of 2^19 6.77 ms; both directions' copies at once are the bound)
     constexpr int64_t kChunk = 1 << 20;
+    constexpr int NS = interp::kHostSlots;
     const int s = h->s;
     const int64_t slot_floats = kChunk * (s + 1 + s);     // points, values, gradients
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    for (int i = 0; i < NS && e == cudaSuccess; ++i) {
         if (!h->stage[i]) e = cudaMalloc(&h->stage[i], (size_t)slot_floats * sizeof(float));
         if (e == cudaSuccess && !h->hs[i]) e = cudaStreamCreateWithFlags(&h->hs[i], cudaStreamNonBlocking);
     }
-    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+    for (int i = 0; i < NS + 1 && e == cudaSuccess; ++i)
         if (!h->hev[i]) e = cudaEventCreateWithFlags(&h->hev[i], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -702,11 +708,11 @@ interp_status interp_eval_host(interp_t *h, const float *pts, int64_t npts, floa
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the internal streams start after the work already on `stream`
-    e = cudaEventRecord(h->hev[2], st);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(h->hs[i], h->hev[2], 0);
+    e = cudaEventRecord(h->hev[NS], st);
+    for (int i = 0; i < NS && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(h->hs[i], h->hev[NS], 0);
     int64_t chunk = 0;
     for (int64_t q0 = 0; q0 < npts && e == cudaSuccess; q0 += kChunk, ++chunk) {
-        const int slot = (int)(chunk & 1);
+        const int slot = (int)(chunk % NS);
         cudaStream_t ss = h->hs[slot];
         const int64_t m = std::min<int64_t>(kChunk, npts - q0);
         float *dp = h->stage[slot], *dv = dp + kChunk * s, *dg = dv + kChunk;
@@ -717,8 +723,8 @@ interp_status interp_eval_host(interp_t *h, const float *pts, int64_t npts, floa
         if (e == cudaSuccess && grad)
             e = cudaMemcpyAsync(grad + q0 * s, dg, (size_t)m * s * sizeof(float), cudaMemcpyDeviceToHost, ss);
     }
-    // `stream` continues after both internal streams
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    // `stream` continues after every internal stream
+    for (int i = 0; i < NS && e == cudaSuccess; ++i) {
         e = cudaEventRecord(h->hev[i], h->hs[i]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->hev[i], 0);
     }
