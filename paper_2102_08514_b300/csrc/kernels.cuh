@@ -459,6 +459,68 @@ __device__ __forceinline__ void eval_piece(const Fold<SP::S> &f, const DevVol<CT
     }
 }
 
+// steps 4-5 for the run-time piece j from the dense tables (splines with SP::DENSE): one loop over
+// the piece's stencil sites gathers c_m and adds c_m A_j[:, m] (uniform float4 loads) to b, so the
+// pieces share one small copy of the code.  b accumulates over the sites in the same order as
+// eval_piece and a zero entry leaves it unchanged, so both give the same sums.
+template <class SP, bool GRAD, class CT>
+__device__ __forceinline__ void eval_piece_dense(const Fold<SP::S> &f, const DevVol<CT> &v, int j, float &val,
+                                                 float (&grad)[SP::S])
+{
+    constexpr int S = SP::S;
+    constexpr int NM = SP::NMON;
+    constexpr int NM4 = (NM + 3) / 4;
+    static_assert(NM <= 120, "the dense path evaluates b for all monomials at once");
+    const CT *cb = v.c + f.base;
+    const float4 *A = SP::dense_a(j);
+    const signed char *g = SP::dense_site(j);
+    const int ns = SP::dense_ns(j);
+    float b[NM];
+    sfor<NM>([&](auto Z) { b[Z] = 0.0f; });
+#pragma unroll 1
+    for (int m = 0; m < ns; ++m) {
+        int off = 0;
+        sfor<S>([&](auto Ax) { off += slot_term(f.sl[Ax], (int)__ldg(g + m * S + Ax)); });
+        const float cm = load_coef<CT>(cb + off);
+        sfor<NM4>([&](auto Q) {
+            constexpr int q = decltype(Q)::value;
+            const float4 a4 = __ldg(A + m * NM4 + q);
+            b[4 * q] = fmaf(a4.x, cm, b[4 * q]);
+            if constexpr (4 * q + 1 < NM) b[4 * q + 1] = fmaf(a4.y, cm, b[4 * q + 1]);
+            if constexpr (4 * q + 2 < NM) b[4 * q + 2] = fmaf(a4.z, cm, b[4 * q + 2]);
+            if constexpr (4 * q + 3 < NM) b[4 * q + 3] = fmaf(a4.w, cm, b[4 * q + 3]);
+        });
+    }
+    const float *an = SP::dense_anchor(j);
+    float t[S];
+    sfor<S>([&](auto Ax) { t[Ax] = f.t[Ax] - __ldg(an + Ax); });
+    constexpr int DEG = SP::DEG;
+    if constexpr (!GRAD) {
+        val += horner<S, S, DEG, 0, NM>(b, t);
+    } else {
+        const VG<S> r = horner_grad<S, S, DEG, 0, NM>(b, t);
+        val += r.v;
+        sfor<S>([&](auto Ax) {
+            const float gs = (f.sl[Ax].sg < 0) ? -r.g[Ax] : r.g[Ax];
+            sfor<S>([&](auto B) { grad[B] += (f.sl[Ax].ax == B) ? gs : 0.0f; });
+        });
+    }
+}
+
+// one binned item of piece j: the dense path or the piece's unrolled code
+template <class SP, bool GRAD, class CT, bool DENSE>
+__device__ __forceinline__ void eval_item(const Fold<SP::S> &f, const DevVol<CT> &v, int j, float &val,
+                                          float (&grad)[SP::S])
+{
+    if constexpr (DENSE) {
+        eval_piece_dense<SP, GRAD, CT>(f, v, j, val, grad);
+    } else {
+        sfor<SP::K>([&](auto Jc) {
+            if (j == decltype(Jc)::value) eval_piece<SP, decltype(Jc)::value, GRAD, CT>(f, v, val, grad);
+        });
+    }
+}
+
 template <class SP, bool GRAD, class CT>
 __device__ __forceinline__ void eval_point(const float (&x)[SP::S], const DevVol<CT> &v, float &val,
                                            float (&grad)[SP::S])
@@ -881,7 +943,7 @@ __device__ __forceinline__ void bin_tile(const float *__restrict__ pts, int64_t 
 // T queries per tile, NT threads per CTA.  With NT = 512 and a large tile the CTA fills an SM,
 // and its warps walk through the sorted pieces together, so only one or two pieces' code is hot
 // in the instruction caches at a time.
-template <class SP, class CT, int MODE, int T, int NT>
+template <class SP, class CT, int MODE, int T, int NT, bool DENSE = false>
 __global__ void __launch_bounds__(NT) k_eval_binned(const float *__restrict__ pts, int64_t n, DevVol<CT> v,
                                                     float *__restrict__ out, float *__restrict__ grad,
                                                     const float *__restrict__ gout)
@@ -909,9 +971,7 @@ __global__ void __launch_bounds__(NT) k_eval_binned(const float *__restrict__ pt
         const Fold<S> f = unpack_rec<SP, CT>(rec[i], v);
         float val = 0.0f, g[S];
         sfor<S>([&](auto A) { g[A] = 0.0f; });
-        sfor<K>([&](auto Jc) {
-            if (j == decltype(Jc)::value) eval_piece<SP, decltype(Jc)::value, GRAD, CT>(f, v, val, g);
-        });
+        eval_item<SP, GRAD, CT, DENSE>(f, v, j, val, g);
         acc[i * NV] = val;
         if constexpr (GRAD) sfor<S>([&](auto A) { acc[i * NV + 1 + A] = g[A]; });
     }
@@ -979,7 +1039,7 @@ __global__ void __launch_bounds__(NT) k_adjoint_binned(const float *__restrict__
 // launches it only for steps <= T); the samples come from the ray geometry, are classified and
 // sorted by piece as in k_eval_binned, evaluated in piece order, and summed per ray in step order
 // and coset order -- the order of k_rays, so both kernels return the same sums.  One CTA per tile.
-template <class SP, bool GRAD, int T, int NT>
+template <class SP, bool GRAD, int T, int NT, bool DENSE = false>
 __global__ void __launch_bounds__(NT) k_rays_binned(RayGeom rg, DevVol<float> v, float *__restrict__ out,
                                                     float *__restrict__ pts_out)
 {
@@ -1028,9 +1088,7 @@ __global__ void __launch_bounds__(NT) k_rays_binned(RayGeom rg, DevVol<float> v,
         const Fold<S> f = unpack_rec<SP, float>(rec[i], v);
         float val = 0.0f, g[S];
         sfor<S>([&](auto A) { g[A] = 0.0f; });
-        sfor<K>([&](auto Jc) {
-            if (j == decltype(Jc)::value) eval_piece<SP, decltype(Jc)::value, GRAD, float>(f, v, val, g);
-        });
+        eval_item<SP, GRAD, float, DENSE>(f, v, j, val, g);
         acc[i * NV] = val;
         if constexpr (GRAD) sfor<S>([&](auto A) { acc[i * NV + 1 + A] = g[A]; });
     }

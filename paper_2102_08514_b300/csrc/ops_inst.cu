@@ -37,13 +37,13 @@ inline unsigned grid_for(int64_t n) { return (unsigned)((n + kTPB - 1) / kTPB); 
 constexpr size_t kMaxSmem = 227 * 1024;
 
 // piece-binned kernel configurations: (tile of queries, threads per CTA)
-template <class CT, int MODE, int T, int NT>
+template <class CT, int MODE, int T, int NT, bool DENSE = false>
 [[maybe_unused]] cudaError_t launch_binned_cfg(const float *pts, int64_t n, const void *c, const ibl::Layout &L,
                                                float *out, float *grad, const float *gout, cudaStream_t st)
 {
     constexpr size_t smem = ib::binned_smem_bytes<SP, MODE, T>();
     static_assert(smem <= kMaxSmem, "binned tile must fit shared memory");
-    auto kern = ib::k_eval_binned<SP, CT, MODE, T, NT>;
+    auto kern = ib::k_eval_binned<SP, CT, MODE, T, NT, DENSE>;
     static unsigned long long configured = 0;          // per device: the attribute is set once
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -85,6 +85,15 @@ template <class CT, int MODE>
         // INTERP_B300_BINCFG=small selects 256-query tiles on 128-thread CTAs (several CTAs per SM)
         const char *cfg = std::getenv("INTERP_B300_BINCFG");
         if (cfg && cfg[0] == 's') return launch_binned_cfg<CT, MODE, 256, 128>(pts, n, c, L, out, grad, gout, st);
+        if constexpr (SP::DENSE) {
+            // the dense piece tables (one shared code path for all pieces) are slower here than the
+            // unrolled per-piece code, whose 1.8x fewer FMAs outweigh its instruction fetch
+            // (measured, BCC V_2, 2^24 random queries: value 5.65 vs 8.67 ms, value+grad 6.81 vs
+            // 9.99 ms); INTERP_B300_DENSE=1 selects them
+            const char *dn = std::getenv("INTERP_B300_DENSE");
+            if (dn && dn[0] == '1')
+                return launch_binned_cfg<CT, MODE, bin_tile<MODE>(), 512, true>(pts, n, c, L, out, grad, gout, st);
+        }
         return launch_binned_cfg<CT, MODE, bin_tile<MODE>(), 512>(pts, n, c, L, out, grad, gout, st);
     } else {
         return cudaErrorInvalidValue;
@@ -171,13 +180,22 @@ template <bool GRAD>
             if (want && rg.steps >= 1 && rg.steps <= T) {
                 constexpr size_t smem = ib::binned_smem_bytes<SP, GRAD ? 1 : 0, T>();
                 static_assert(smem <= kMaxSmem, "binned tile must fit shared memory");
-                auto kern = ib::k_rays_binned<SP, GRAD, T, 512>;
-                static unsigned long long configured = 0;
+                // rays of a dense-table spline use the tables (measured, BCC V_2, 1024^2 x 256: value
+                // 127 -> 104 ms, value+grad 151 -> 104 ms); INTERP_B300_DENSE=0 selects the
+                // unrolled code
+                const char *dn = std::getenv("INTERP_B300_DENSE");
+                const bool dense = SP::DENSE && (!dn || dn[0] != '0');
+                auto kd = ib::k_rays_binned<SP, GRAD, T, 512, SP::DENSE>;
+                auto kp = ib::k_rays_binned<SP, GRAD, T, 512>;
+                auto kern = dense ? kd : kp;
+                static unsigned long long configured = 0;       // both variants, once per device
                 int dev = 0;
                 cudaError_t e = cudaGetDevice(&dev);
                 if (e != cudaSuccess) return e;
                 if (dev >= 64 || !(configured >> dev & 1ull)) {
-                    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    e = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    if (e == cudaSuccess && SP::DENSE)
+                        e = cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                     if (e != cudaSuccess) return e;
                     if (dev < 64) configured |= 1ull << dev;
                 }

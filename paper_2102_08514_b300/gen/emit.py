@@ -36,6 +36,14 @@ BATCH_3D = {"bcc_linear", "bcc_quintic", "fcc_6dir", "cc_7dir", "bcc_quartic", "
 MAX_PIECES, MAX_PACKED, MAX_Q = 15, 64, 12
 
 
+def dense_pieces(T, nz_lists) -> bool:
+    """Splines for which dense device tables of A_j are emitted (one shared loop over the sites
+    instead of one unrolled code block per piece): many pieces with many nonzeros, whose unrolled
+    code does not fit the instruction caches.  The binned rays kernel uses them; the binned
+    evaluation of random queries keeps the unrolled code (measured faster)."""
+    return len(T.pieces) >= 8 and max(len(z) for z in nz_lists) >= 400
+
+
 def analyse_entry(name):
     """The generator's tables for a built-in name (box spline or Voronoi spline)."""
     if name in VORONOI:
@@ -110,6 +118,28 @@ def emit_struct(T, half_storage: bool = True) -> tuple[str, dict]:
     if T.r > MAX_PACKED:
         # sigma as a byte table in device memory (read through the read-only cache)
         L.append(f"static __device__ const unsigned char {T.name}_sigma_tab[{T.r}] = {_arr(T.sigma)};")
+    dense = dense_pieces(T, nz_lists)
+    if dense:
+        # A_j dense, site-major, monomials padded to a multiple of 4 (float4 loads), zero columns
+        # past the piece's own sites; the sites, their count and the anchors per piece
+        nm4 = (nmon + 3) // 4
+        vals = []
+        for j, z in enumerate(nz_lists):
+            A = [[Fr(0)] * (nm4 * 4) for _ in range(nsmax)]
+            for m, a, v in z:
+                A[m][a] = v
+            for row in A:
+                vals.extend(row)
+        L.append(f"static __device__ const float __align__(16) {T.name}_dense_a[{len(vals)}] = "
+                 f"{_arr(vals, f32_hex)};")
+        sites = []
+        for pc in T.pieces:
+            for m in range(nsmax):
+                sites.extend(pc.sites[m] if m < len(pc.sites) else [0] * s)
+        L.append(f"static __device__ const signed char {T.name}_dense_site[{len(sites)}] = {_arr(sites)};")
+        L.append(f"static __device__ const int {T.name}_dense_ns[{K}] = {_arr([len(pc.sites) for pc in T.pieces])};")
+        L.append(f"static __device__ const float {T.name}_dense_anchor[{K * s}] = "
+                 f"{_arr([a for pc in T.pieces for a in pc.anchor], f32_hex)};")
     L.append(f"struct {T.name} {{")
     L.append(f'    static constexpr const char* NAME = "{T.name}";')
     L.append(f"    static constexpr int S = {s}, NXI = {len(T.xi[0])}, M = {M}, D = {T.D}, DETL = {T.det_l};")
@@ -130,6 +160,13 @@ def emit_struct(T, half_storage: bool = True) -> tuple[str, dict]:
     L.append(f"    static constexpr int SIGMA[R] = {_arr(T.sigma)};")
     if T.r > MAX_PACKED:
         L.append(f"    __device__ static unsigned sigma_at(unsigned q) {{ return __ldg(&{T.name}_sigma_tab[q]); }}")
+    L.append(f"    static constexpr bool DENSE = {'true' if dense else 'false'};  // dense A_j tables emitted")
+    if dense:
+        L.append(f"    __device__ static const float4 *dense_a(int j) {{ return reinterpret_cast<const float4 *>("
+                 f"{T.name}_dense_a) + j * {nsmax * ((nmon + 3) // 4)}; }}")
+        L.append(f"    __device__ static const signed char *dense_site(int j) {{ return {T.name}_dense_site + j * {nsmax * s}; }}")
+        L.append(f"    __device__ static int dense_ns(int j) {{ return __ldg(&{T.name}_dense_ns[j]); }}")
+        L.append(f"    __device__ static const float *dense_anchor(int j) {{ return {T.name}_dense_anchor + j * {s}; }}")
     L.append(f"    static constexpr int NS[K] = {_arr([len(pc.sites) for pc in T.pieces])};")
     L.append(f"    static constexpr int NNZ[K] = {_arr([len(z) for z in nz_lists])};")
     L.append(f"    static constexpr float ANCHOR[K][S] = {_arr([_arr(pc.anchor, f32_hex) for pc in T.pieces])};")

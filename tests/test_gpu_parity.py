@@ -263,7 +263,7 @@ def test_full_size_headline_workload_sampled():
     assert np.abs(grad.cpu().numpy()[idx] - ref_g).max() <= VALUE_TOL * cmax * G
 
 
-@pytest.mark.parametrize("name", ["fcc_6dir", "d4s_8dir", "d4_8dir", "bcc_voronoi1", "fcc_voronoi2"])
+@pytest.mark.parametrize("name", ["fcc_6dir", "d4s_8dir", "d4_8dir", "bcc_voronoi1", "fcc_voronoi2", "bcc_voronoi2"])
 def test_piece_binned_kernel_equals_plain_kernel(name, monkeypatch):
     # multi-piece splines run a piece-binned kernel by default; INTERP_B300_BINNED=0 selects the
     # plain one: same sums in the same order, so the results agree exactly
