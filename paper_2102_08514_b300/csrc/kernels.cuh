@@ -723,8 +723,9 @@ __device__ __forceinline__ void batch_dispatch(int kind, const BatchVol &bv, int
 // item ids are ordered volume by volume; a CTA finds its volume by binary search over the
 // per-volume first-tile prefix.  The counter is zeroed before each launch (a memset node of the
 // same graph); the loop ends when the counter passes the total, so it always terminates.
+// Five resident CTAs per SM (96 registers, no spills; unbounded it takes 121 and four).
 template <class... SPs>
-__global__ void __launch_bounds__(128) k_batch(const BatchVol *__restrict__ vols, int nvol, int64_t total_tiles,
+__global__ void __launch_bounds__(128, 5) k_batch(const BatchVol *__restrict__ vols, int nvol, int64_t total_tiles,
                                                unsigned long long *__restrict__ counter)
 {
     __shared__ long long item;
