@@ -125,7 +125,7 @@ def test_adjoint_parity(name):
 
 
 @pytest.mark.parametrize("name", ["bcc_linear", "cc_linear_rd", "cc_voronoi1", "bcc_voronoi1", "fcc_voronoi1"])
-def test_gradient_at_exact_ties(name):
+def test_gradient_at_exact_ties(name, monkeypatch):
     # continuous, not C^1 splines: at points exactly on mesh planes (integer, half and quarter
     # coordinates, and sums of them) the gradient is the one-sided limit along the fixed world
     # direction v = (1, 2^-12, 2^-24), on the GPU (every coset and fold decision) as in the oracle
@@ -141,12 +141,8 @@ def test_gradient_at_exact_ties(name):
     pts[::3, 1] = (np.round(rng.uniform(lo[1], hi[1], 500) * 2 ** 12) / 2 ** 12).astype(np.float32)
     pts[1::3, 0] = (np.floor(pts[1::3, 1]) + 0.5 - (pts[1::3, 1] - np.floor(pts[1::3, 1]))).astype(np.float32)
     for flag in ("1", "0") if SPLINES[name].order else ("0",):
-        import os
-        os.environ["INTERP_B300_BINNED"] = flag
-        try:
-            val, grad = itp.eval_grad(torch.from_numpy(pts).cuda())
-        finally:
-            os.environ.pop("INTERP_B300_BINNED")
+        monkeypatch.setenv("INTERP_B300_BINNED", flag)         # binned and plain kernels alike
+        val, grad = itp.eval_grad(torch.from_numpy(pts).cuda())
         ref_v, ref_g = OracleSpline(name).eval_sum(lat.D, lat.cosets, c, pts, grad=True)
         cmax = np.abs(c).max()
         G = grad_bound(name, pts[:16])
