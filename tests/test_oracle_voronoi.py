@@ -178,3 +178,28 @@ def test_gradient_at_exact_ties_is_the_one_sided_limit(name):
     f1, g1 = o.eval_sum(lat.D, lat.cosets, c, x + 2.0 ** -36 * v, grad=True)
     assert np.abs(f0 - f1).max() < 1e-9
     assert np.abs(g0 - g1).max() < 1e-9
+
+
+def test_table1_voronoi_rows(golden_dir):
+    # Table 1's Voronoi rows on their own lattices: '# Lookups' (sites whose shifted basis is
+    # nonzero at a generic point) and 'Order' (discrete moments constant below it, Strang-Fix)
+    import itertools, json, os
+    rows = json.load(open(os.path.join(golden_dir, "table1_lookups.json")))["voronoi_rows"]
+    rng = np.random.default_rng(41)
+    for row in rows:
+        lat, gens, order = _spec(row["spline"])
+        v = oracle.VoronoiSpline(lat.L, gens, order)
+        assert order == row["order"] - 1                       # V_n has order n + 1
+        xs = np.round(rng.uniform(-1, 1, (4, 3)) * 2 ** 18) / 2 ** 18
+        betas = [b for d in range(row["order"] + 1) for b in itertools.product(range(d + 1), repeat=3) if sum(b) == d]
+        moments = {}
+        for x in xs:
+            sites = oracle.lattice_sites(lat.L, x - v.halfwidth - 1, x + v.halfwidth + 1).astype(np.float64)
+            w = v.phi(x - sites)
+            assert int((w > 0).sum()) == row["lookups"], row["name"]
+            for b in betas:
+                moments.setdefault(b, []).append(np.sum(w * np.prod((sites - x) ** np.asarray(b), axis=1)))
+        for b, m in moments.items():
+            if sum(b) < row["order"]:
+                assert np.ptp(m) < 1e-9, (row["name"], b)
+        assert max(np.ptp(m) for b, m in moments.items() if sum(b) == row["order"]) > 1e-6, row["name"]
