@@ -208,7 +208,7 @@ def run_batch(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded; uniform)",
         "config": {"workload": f"batch64: 64 volumes (edge lengths log-uniform in 32..256, splines bcc_linear / "
                                f"bcc_quintic / fcc_6dir / cc_7dir in turn) x 2^20 queries + d4s_8dir 2 x 48^4 x "
-                               f"2^24 queries, one persistent launch per dimension replayed from a CUDA graph",
+                               f"2^24 queries, one persistent launch for the 3-D volumes and one piece-binned launch for the 4-D one, replayed from a CUDA graph",
                    "queries": total_q, "tiles": tiles},
         "gpu_launches": 2 * args.steps, "clocks": clk.summary(),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
