@@ -54,6 +54,27 @@ def peaks():
         return {"hbm_gbs": 6400.0, "sm_max_mhz": SM_MAX_MHZ}, "fallback"
 
 
+def presort_applies(info, n: int) -> bool:
+    """Whether an evaluation call of n queries takes the library's piece pre-sort: its default for
+    this spline (interp_info_t.presort) at >= 2^16 queries, or INTERP_B300_PRESORT=0 / 1 (any
+    multi-piece spline)."""
+    env = os.environ.get("INTERP_B300_PRESORT")
+    if env:
+        return env[0] == "1" and info.n_pieces >= 4
+    return bool(info.presort) and n >= (1 << 16)
+
+
+def launches_per_step(form: str, n: int, presort: bool) -> int:
+    """This library's kernels in one step: the evaluation kernel (value forms), or the adjoint
+    kernel and the unpadding add (adjoint); with the pre-sort, per chunk of 2^21 queries the piece
+    classifier, count, scan and scatter kernels before the evaluation (adjoint) kernel, and the
+    un-permute after it (value forms)."""
+    chunks = -(-n // (1 << 21))
+    if form == "adjoint":
+        return (5 * chunks if presort else 1) + 1
+    return 6 * chunks if presort else 1
+
+
 def fp32_peak_tflops():
     # derived: SMs x FP32 lanes x 2 FLOP per FMA x max SM clock
     return SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
@@ -465,6 +486,9 @@ def run_ours(args):
     peak = fp32_peak_tflops()
     kname = f"k_eval<{wl.spline},{args.storage},{form}>" if form != "adjoint" else f"k_adjoint<{wl.spline}>"
     traffic, l1l2_frac = recorded_capture(kname)
+    presort = presort_applies(info, n)
+    if presort:
+        kname += " after the piece pre-sort (whole call timed)"
     line = {
         "metric": METRIC,
         "value": value,
@@ -491,7 +515,7 @@ def run_ours(args):
                                "both_directions_at_once_ms": both_ms, "frac_of_both": both_ms / e2e_ms,
                                "note": "plain pinned copies of the step's bytes: the larger of the two directions "
                                        "alone, and both directions at once on two streams"}},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * launches_per_step(form, n, presort),
         "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": kname,

@@ -371,6 +371,189 @@ struct interp {
     cudaEvent_t hev[kHostSlots + 1] = {};
 };
 
+// ------------------------------------------------------------------------------------ piece pre-sort
+//
+// The piece-binned kernels sort a tile's (query, coset) items by piece (Sec. 4.3's sub-regions)
+// in shared memory, but a tile of random queries still meets every piece, so each tile streams
+// the code of all K unrolled pieces.  Where those pieces together far exceed the instruction
+// caches (BCC V_2: 14 pieces of ~1000 immediate FMAs per coset), the queries are first sorted
+// across the whole call by the pieces of their first cosets (a device-wide counting sort), the
+// binned kernel runs on the sorted points, and the results go back to the callers' positions.
+// A query's sum does not depend on which other queries share its tile, so the values are the
+// binned kernel's bit for bit.  Scratch comes from a stream-ordered pool per call (calls on one
+// handle may run concurrently on several streams); under stream capture, or when the scratch
+// cannot be had, the call runs the binned kernel on the unsorted points instead.
+
+namespace {
+
+constexpr int kPsMaxKeys = 1024;           // keys: the pieces of the first c cosets, K^c <= 1024
+constexpr int64_t kPsChunk = 1 << 21;      // queries sorted at a time (the scratch stays near L2 size)
+constexpr int kPsBlock = 4096;             // queries per CTA of the scatter
+
+// key of each query (mixed radix K over the pieces of its first c cosets) and the keys' totals
+__global__ void __launch_bounds__(256) k_ps_count(const int32_t *__restrict__ piece, int n, int M, int c, int K,
+                                                  int nkeys, uint16_t *__restrict__ key, unsigned *__restrict__ total)
+{
+    __shared__ unsigned hist[kPsMaxKeys];
+    for (int i = threadIdx.x; i < nkeys; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        unsigned k = 0;
+        for (int j = 0; j < c; ++j) k = k * K + min((unsigned)piece[(int64_t)q * M + j], (unsigned)(K - 1));
+        key[q] = (uint16_t)k;
+        atomicAdd(&hist[k], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nkeys; i += blockDim.x)
+        if (hist[i]) atomicAdd(&total[i], hist[i]);
+}
+
+// exclusive prefix sum of the totals into the cursors; zeroes the totals for the next chunk
+__global__ void __launch_bounds__(kPsMaxKeys) k_ps_scan(unsigned *__restrict__ total, unsigned *__restrict__ cursor,
+                                                         int nkeys)
+{
+    __shared__ unsigned s[kPsMaxKeys];
+    const int t = threadIdx.x;
+    const unsigned v = t < nkeys ? total[t] : 0u;
+    s[t] = v;
+    __syncthreads();
+    for (int off = 1; off < kPsMaxKeys; off <<= 1) {
+        const unsigned a = t >= off ? s[t - off] : 0u;
+        __syncthreads();
+        s[t] += a;
+        __syncthreads();
+    }
+    if (t < nkeys) {
+        cursor[t] = s[t] - v;
+        total[t] = 0;
+    }
+}
+
+// each CTA reserves, per key, a range of the chunk's sorted order for its kPsBlock queries and
+// copies them there (a CTA-local sort before the copy, for contiguous stores, measured no faster)
+template <int S>
+__global__ void __launch_bounds__(256) k_ps_scatter(const float *__restrict__ pts, const float *__restrict__ gout,
+                                                    const uint16_t *__restrict__ key, int n, int nkeys,
+                                                    unsigned *__restrict__ cursor, int32_t *__restrict__ perm,
+                                                    float *__restrict__ pts_s, float *__restrict__ gout_s)
+{
+    __shared__ unsigned cnt[kPsMaxKeys], base[kPsMaxKeys];
+    for (int i = threadIdx.x; i < nkeys; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    const int q0 = blockIdx.x * kPsBlock, q1 = min(n, q0 + kPsBlock);
+    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) atomicAdd(&cnt[key[q]], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nkeys; i += blockDim.x) {
+        const unsigned c = cnt[i];
+        base[i] = c ? atomicAdd(&cursor[i], c) : 0u;
+        cnt[i] = 0;
+    }
+    __syncthreads();
+    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+        const unsigned k = key[q];
+        const unsigned p = base[k] + atomicAdd(&cnt[k], 1u);
+        perm[p] = q;
+#pragma unroll
+        for (int a = 0; a < S; ++a) pts_s[(int64_t)p * S + a] = pts[(int64_t)q * S + a];
+        if (gout) gout_s[p] = gout[q];
+    }
+}
+
+// results of the sorted queries back to their callers' positions
+template <int S>
+__global__ void __launch_bounds__(256) k_ps_unpermute(const int32_t *__restrict__ perm, int n,
+                                                      const float *__restrict__ out_s, const float *__restrict__ grad_s,
+                                                      float *__restrict__ out, float *__restrict__ grad)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int q = perm[i];
+    if (out) out[q] = out_s[i];
+    if (grad) {
+#pragma unroll
+        for (int a = 0; a < S; ++a) grad[(int64_t)q * S + a] = grad_s[(int64_t)i * S + a];
+    }
+}
+
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+
+// the per-device pool of the pre-sort scratch (kept up to 1 GiB between calls)
+cudaError_t ps_pool(int dev, cudaMemPool_t *out)
+{
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps p = {};
+        p.allocType = cudaMemAllocationTypePinned;
+        p.location.type = cudaMemLocationTypeDevice;
+        p.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        cudaError_t e = cudaMemPoolCreate(&pool, &p);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = 1ull << 30;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        g_pool[dev] = pool;
+    }
+    *out = g_pool[dev];
+    return cudaSuccess;
+}
+
+// whether a call of npts queries (at least 2^16) takes the pre-sort.  Measured on 2^24 random
+// queries, sort included: faster for many large pieces (K >= 8 pieces of >= 500 FMAs per coset:
+// BCC V_2, value 5.76 -> 3.19 ms, value+grad 6.95 -> 3.89 ms, adjoint 7.88 -> 3.57 ms) and for
+// the 8-coset D4 spline, whose gathers come from DRAM (value 19.3 -> 18.1 ms, value+grad
+// 19.7 -> 16.7 ms); slower for D4* (value 3.37 -> 3.91 ms: its 6 pieces' code is amortised
+// within the tiles already, the sort is not) and no faster for BCC V_1 or FCC V_2, whose pieces
+// fit the instruction caches.  INTERP_B300_PRESORT=0 / 1 forces it off / on.
+bool presort_default(const SplineOps *ops)
+{
+    return (ops->K >= 8 && ops->fma_value / ops->M >= 500.0) || (ops->M >= 8 && ops->K >= 4);
+}
+
+bool presort_wanted(const SplineOps *ops, int64_t npts)
+{
+    const char *e = std::getenv("INTERP_B300_PRESORT");
+    if (e) return e[0] == '1';
+    return npts >= (1 << 16) && presort_default(ops);
+}
+
+struct PresortWs {
+    void *block = nullptr;
+    int32_t *piece = nullptr, *perm = nullptr;
+    uint16_t *key = nullptr;
+    float *pts_s = nullptr, *gout_s = nullptr, *out_s = nullptr, *grad_s = nullptr;
+    unsigned *total = nullptr, *cursor = nullptr;
+    int c = 1, nkeys = 1;
+};
+
+// scratch for chunks of up to min(npts, kPsChunk) queries on `st`; false (error cleared) when the
+// stream is capturing or the pool has no room
+bool ps_acquire(const interp *h, int64_t npts, cudaStream_t st, PresortWs &w);
+void ps_release(PresortWs &w, cudaStream_t st)
+{
+    if (w.block) cudaFreeAsync(w.block, st);
+    w.block = nullptr;
+}
+
+// sort chunk [pts, pts + m) (and its gout) by key: fills w.perm, w.pts_s (and w.gout_s)
+cudaError_t ps_sort_chunk(const interp *h, PresortWs &w, const float *pts, const float *gout, int m, cudaStream_t st);
+cudaError_t ps_unpermute(int s, const PresortWs &w, int m, float *out, float *grad, cudaStream_t st)
+{
+    const unsigned grid = (unsigned)((m + 255) / 256);
+    if (s == 3)
+        k_ps_unpermute<3><<<grid, 256, 0, st>>>(w.perm, m, w.out_s, w.grad_s, out, grad);
+    else
+        k_ps_unpermute<4><<<grid, 256, 0, st>>>(w.perm, m, w.out_s, w.grad_s, out, grad);
+    return cudaPeekAtLastError();
+}
+
+}  // namespace
+
 static cudaError_t eval_launch(const interp *h, const float *pts, int64_t npts, float *out, float *grad, const float *gout,
                         int mode, cudaStream_t st)
 {
@@ -381,8 +564,105 @@ static cudaError_t eval_launch(const interp *h, const float *pts, int64_t npts, 
     const char *bn = std::getenv("INTERP_B300_BINNED");
     const bool want = bn ? bn[0] == '1' : h->ops->K >= 4;
     const bool binned = want && h->ops->eval_binned[dt][mode];
-    return (binned ? h->ops->eval_binned : h->ops->eval)[dt][mode](pts, npts, h->coeffs, h->lay, out, grad, gout, st);
+    const ibr::EvalFn fn = (binned ? h->ops->eval_binned : h->ops->eval)[dt][mode];
+    PresortWs w;
+    if (!binned || !presort_wanted(h->ops, npts) || !ps_acquire(h, npts, st, w))
+        return fn(pts, npts, h->coeffs, h->lay, out, grad, gout, st);
+    const int s = h->s;
+    cudaError_t e = cudaSuccess;
+    for (int64_t q0 = 0; q0 < npts && e == cudaSuccess; q0 += kPsChunk) {
+        const int m = (int)std::min<int64_t>(kPsChunk, npts - q0);
+        e = ps_sort_chunk(h, w, pts + q0 * s, mode == 2 ? gout + q0 : nullptr, m, st);
+        // value (and gradient) of the sorted queries; the pullback (mode 2) writes w * grad only
+        if (e == cudaSuccess)
+            e = fn(w.pts_s, m, h->coeffs, h->lay, mode == 2 ? nullptr : w.out_s, mode >= 1 ? w.grad_s : nullptr,
+                   mode == 2 ? w.gout_s : nullptr, st);
+        if (e == cudaSuccess)
+            e = ps_unpermute(s, w, m, mode == 2 || !out ? nullptr : out + q0, mode >= 1 ? grad + q0 * s : nullptr, st);
+    }
+    ps_release(w, st);
+    return e;
 }
+
+// dL/dc into h->dpad; multi-piece splines with large pieces take the pre-sort like eval_launch
+// (the adjoint's atomic scatter has no fixed summation order either way)
+static cudaError_t adjoint_launch(const interp *h, const float *pts, int64_t npts, const float *gout, cudaStream_t st)
+{
+    PresortWs w;
+    if (h->ops->K < 4 || !presort_wanted(h->ops, npts) || !ps_acquire(h, npts, st, w))
+        return h->ops->adjoint(pts, npts, gout, h->lay32, h->dpad, st);
+    const int s = h->s;
+    cudaError_t e = cudaSuccess;
+    for (int64_t q0 = 0; q0 < npts && e == cudaSuccess; q0 += kPsChunk) {
+        const int m = (int)std::min<int64_t>(kPsChunk, npts - q0);
+        e = ps_sort_chunk(h, w, pts + q0 * s, gout + q0, m, st);
+        if (e == cudaSuccess) e = h->ops->adjoint(w.pts_s, m, w.gout_s, h->lay32, h->dpad, st);
+    }
+    ps_release(w, st);
+    return e;
+}
+
+namespace {
+
+bool ps_acquire(const interp *h, int64_t npts, cudaStream_t st, PresortWs &w)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return false;
+    }
+    const SplineOps *ops = h->ops;
+    w.c = 1;
+    w.nkeys = ops->K;
+    while (w.c < ops->M && w.nkeys * ops->K <= kPsMaxKeys) {
+        ++w.c;
+        w.nkeys *= ops->K;
+    }
+    if (w.nkeys > kPsMaxKeys) return false;
+    const size_t C = (size_t)std::min<int64_t>(npts, kPsChunk), s = (size_t)h->s;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t sz[] = {up(C * ops->M * 4), up(C * 2), up(C * 4), up(C * s * 4), up(C * 4), up(C * 4),
+                         up(C * s * 4), up((size_t)kPsMaxKeys * 4), up((size_t)kPsMaxKeys * 4)};
+    size_t bytes = 0;
+    for (size_t b : sz) bytes += b;
+    cudaMemPool_t pool = nullptr;
+    if (ps_pool(h->device, &pool) != cudaSuccess || cudaMallocFromPoolAsync(&w.block, bytes, pool, st) != cudaSuccess) {
+        cudaGetLastError();
+        w.block = nullptr;
+        return false;
+    }
+    unsigned char *p = static_cast<unsigned char *>(w.block);
+    void **dst[] = {(void **)&w.piece, (void **)&w.key,   (void **)&w.perm,  (void **)&w.pts_s, (void **)&w.gout_s,
+                    (void **)&w.out_s, (void **)&w.grad_s, (void **)&w.total, (void **)&w.cursor};
+    for (int i = 0; i < 9; ++i) {
+        *dst[i] = p;
+        p += sz[i];
+    }
+    if (cudaMemsetAsync(w.total, 0, (size_t)kPsMaxKeys * 4, st) != cudaSuccess) {
+        cudaGetLastError();
+        ps_release(w, st);
+        return false;
+    }
+    return true;
+}
+
+cudaError_t ps_sort_chunk(const interp *h, PresortWs &w, const float *pts, const float *gout, int m, cudaStream_t st)
+{
+    const SplineOps *ops = h->ops;
+    cudaError_t e = ops->debug(pts, m, h->lay32, nullptr, w.piece, st);
+    if (e != cudaSuccess) return e;
+    const unsigned gc = (unsigned)std::min<int64_t>((m + 255) / 256, 148 * 8);
+    k_ps_count<<<gc, 256, 0, st>>>(w.piece, m, ops->M, w.c, ops->K, w.nkeys, w.key, w.total);
+    k_ps_scan<<<1, kPsMaxKeys, 0, st>>>(w.total, w.cursor, w.nkeys);
+    const unsigned gs = (unsigned)((m + kPsBlock - 1) / kPsBlock);
+    if (h->s == 3)
+        k_ps_scatter<3><<<gs, 256, 0, st>>>(pts, gout, w.key, m, w.nkeys, w.cursor, w.perm, w.pts_s, w.gout_s);
+    else
+        k_ps_scatter<4><<<gs, 256, 0, st>>>(pts, gout, w.key, m, w.nkeys, w.cursor, w.perm, w.pts_s, w.gout_s);
+    return cudaPeekAtLastError();
+}
+
+}  // namespace
 
 // the handle for a registry entry: validate dims and storage, lay out and zero the padded arrays
 static interp_status create_handle(const SplineOps *ops, const int32_t *dims, interp_dtype storage, interp_t **out)
@@ -531,6 +811,7 @@ interp_status interp_info(const interp_t *h, interp_info_t *info)
     info->coeff_count = h->coeff_count;
     info->name = o.name;
     info->kind = o.kind;
+    info->presort = presort_default(&o) ? 1 : 0;
     return INTERP_OK;
 }
 
@@ -756,7 +1037,7 @@ interp_status interp_backward(interp_t *h, const float *pts, int64_t npts, const
         }
     }
     e = cudaMemsetAsync(h->dpad, 0, dbytes, st);
-    if (e == cudaSuccess) e = h->ops->adjoint(pts, npts, gout, h->lay32, h->dpad, st);
+    if (e == cudaSuccess) e = adjoint_launch(h, pts, npts, gout, st);
     if (e == cudaSuccess) {
         const unsigned grid = (unsigned)std::min<int64_t>((h->coeff_count + 255) / 256, 148 * 32);
         k_unpad_add<<<grid, 256, 0, st>>>(h->dpad, dcoeffs, h->coeff_count, h->lay32);
