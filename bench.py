@@ -639,20 +639,30 @@ def run_reference(args):
     c = coefficients(wl).astype(np.float64)
     lo, hi = interior_box(wl.spline, wl.dims)
     pts = uniform_points(make_rng(wl.seed, 0), 1 << 16, lo, hi).astype(np.float64)
-    # size each step so the whole run takes a few minutes
-    probe = pts[:cores * 2]
-    t = time.perf_counter()
-    orc.eval_sum(spl, lat.D, lat.cosets, c, probe, grad=(form != "value"), nthreads=cores)
-    rate = len(probe) / max(time.perf_counter() - t, 1e-6)
-    per_step = int(max(cores, min(len(pts) // (args.steps + args.warmup + 1), rate * 120.0 / (args.steps + args.warmup))))
-    off = len(probe)
-
-    def step(i):
-        sl = pts[off + (i * per_step) % (len(pts) - off - per_step):][:per_step]
+    def call(sl):
         if form == "adjoint":
             orc.adjoint(spl, lat.D, lat.cosets, c.shape, sl, np.ones(len(sl)))
         else:
             orc.eval_sum(spl, lat.D, lat.cosets, c, sl, grad=(form != "value"), nthreads=cores)
+
+    # size each step so the whole run takes about two and a half minutes.  A call on m queries
+    # costs about a + b m (a: the oracle's fixed cost per call, tens of ms), fitted from two
+    # probes, so the step takes as many queries as its share of the time allows
+    m1, m2 = cores, 8 * cores
+    t = time.perf_counter()
+    call(pts[:m1])
+    t1 = time.perf_counter() - t
+    t = time.perf_counter()
+    call(pts[m1:m1 + m2])
+    t2 = time.perf_counter() - t
+    b = max((t2 - t1) / (m2 - m1), 1e-7)
+    a = max(t1 - b * m1, 0.0)
+    budget = 150.0 / (args.steps + args.warmup)
+    off = m1 + m2
+    per_step = int(min((len(pts) - off) // 2, max(cores, (budget - a) / b)))
+
+    def step(i):
+        call(pts[off + (i * per_step) % (len(pts) - off - per_step):][:per_step])
 
     for i in range(args.warmup):
         step(i)

@@ -141,3 +141,21 @@ def test_presort_default_rule():
     for name, w in want.items():
         itp = make_interpolator(name, (6,) * len(SPLINES[name].xi))
         assert itp.info.presort == w, name
+
+
+def test_presorted_half_storage(monkeypatch):
+    # the pre-sort in front of the FP16-storage binned kernel (BCC V_1 keeps FP16 kernels)
+    name = "bcc_voronoi1"
+    torch = require_cuda()
+    dims = (12, 12, 12)
+    itp = make_interpolator(name, dims, "f16")
+    lat = LATTICES[SPLINES[name].lattice]
+    c = make_rng(82, 3).uniform(-1, 1, (len(lat.cosets),) + dims).astype(np.float32)
+    itp.set_coeffs(torch.from_numpy(c).cuda())
+    pts = torch.from_numpy(mixed_points(name, dims, 70001, 83)).cuda()
+    res = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("INTERP_B300_PRESORT", flag)
+        res.append(itp.eval_grad(pts))
+    for a, b in zip(*res):
+        assert torch.equal(torch.nan_to_num(a, nan=7.0), torch.nan_to_num(b, nan=7.0))
