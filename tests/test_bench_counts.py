@@ -1,0 +1,35 @@
+"""Host logic of bench.py: the kernel launches a step claims (the evaluation kernel, the adjoint
+kernel plus the unpadding add, and with the piece pre-sort six kernels per chunk of 2^21 queries
+for the value forms, five plus the add for the adjoint) and when the pre-sort applies."""
+import os
+import sys
+import types
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_launches_per_step():
+    n = 1 << 24                                        # 8 chunks of 2^21
+    assert bench.launches_per_step("value", n, False) == 1
+    assert bench.launches_per_step("value_grad", n, False) == 1
+    assert bench.launches_per_step("adjoint", n, False) == 2
+    assert bench.launches_per_step("value", n, True) == 48
+    assert bench.launches_per_step("value_grad", n + 1, True) == 54   # a ninth, ragged chunk
+    assert bench.launches_per_step("adjoint", n, True) == 41
+
+
+def test_presort_applies(monkeypatch):
+    monkeypatch.delenv("INTERP_B300_PRESORT", raising=False)
+    on = types.SimpleNamespace(presort=1, n_pieces=14)
+    off = types.SimpleNamespace(presort=0, n_pieces=6)
+    assert bench.presort_applies(on, 1 << 16) and not bench.presort_applies(on, (1 << 16) - 1)
+    assert not bench.presort_applies(off, 1 << 24)
+    monkeypatch.setenv("INTERP_B300_PRESORT", "1")
+    assert bench.presort_applies(off, 10)
+    assert not bench.presort_applies(types.SimpleNamespace(presort=0, n_pieces=1), 1 << 24)
+    monkeypatch.setenv("INTERP_B300_PRESORT", "0")
+    assert not bench.presort_applies(on, 1 << 24)
