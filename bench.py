@@ -645,21 +645,25 @@ def run_reference(args):
         else:
             orc.eval_sum(spl, lat.D, lat.cosets, c, sl, grad=(form != "value"), nthreads=cores)
 
-    # size each step so the whole run takes about two and a half minutes.  A call on m queries
-    # costs about a + b m (a: the oracle's fixed cost per call, tens of ms), fitted from two
-    # probes, so the step takes as many queries as its share of the time allows
-    m1, m2 = cores, 8 * cores
+    # size each step so the whole run takes about two and a half minutes.  The oracle deals
+    # queries to its threads in chunks of 4, so a sample is a multiple of unit = 4 x cores (a
+    # smaller one leaves threads idle); a call on m queries costs about a + b m, fitted from two
+    # probes after an untimed first call, and a step takes as many units as its share allows
+    unit = 4 * cores
+    call(pts[:unit])
+    m1, m2 = unit, 4 * unit
     t = time.perf_counter()
-    call(pts[:m1])
+    call(pts[unit:unit + m1])
     t1 = time.perf_counter() - t
     t = time.perf_counter()
-    call(pts[m1:m1 + m2])
+    call(pts[unit + m1:unit + m1 + m2])
     t2 = time.perf_counter() - t
     b = max((t2 - t1) / (m2 - m1), 1e-7)
     a = max(t1 - b * m1, 0.0)
     budget = 150.0 / (args.steps + args.warmup)
-    off = m1 + m2
-    per_step = int(min((len(pts) - off) // 2, max(cores, (budget - a) / b)))
+    off = unit + m1 + m2
+    units = max(1, int((budget - a) / (b * unit)))
+    per_step = int(min(((len(pts) - off) // 2) // unit * unit, units * unit))
 
     def step(i):
         call(pts[off + (i * per_step) % (len(pts) - off - per_step):][:per_step])
