@@ -66,10 +66,10 @@ def presort_applies(info, n: int) -> bool:
 
 def launches_per_step(form: str, n: int, presort: bool) -> int:
     """This library's kernels in one step: the evaluation kernel (value forms), or the adjoint
-    kernel and the unpadding add (adjoint); with the pre-sort, per chunk of 2^21 queries the piece
+    kernel and the unpadding add (adjoint); with the pre-sort, per chunk of 2^22 queries the piece
     classifier, count, scan and scatter kernels before the evaluation (adjoint) kernel, and the
     un-permute after it (value forms)."""
-    chunks = -(-n // (1 << 21))
+    chunks = -(-n // (1 << 22))
     if form == "adjoint":
         return (5 * chunks if presort else 1) + 1
     return 6 * chunks if presort else 1

@@ -27,7 +27,7 @@
  *     8-coset D4; interp_info_t.presort says which), eval, eval_grad and interp_backward calls
  *     of 2^16 or more queries first sort the queries
  *     on the device by the pieces (Sec. 4.3's sub-regions) of their first cosets, in chunks of
- *     2^21, so that the piece-binned kernel runs one piece's code for long stretches; results go
+ *     2^22, so that the piece-binned kernel runs one piece's code for long stretches; results go
  *     back to the callers' positions.  Values and gradients are the same bits as without the
  *     sort.  The scratch (at most ~80 bytes per query of a chunk) comes per call from a
  *     stream-ordered memory pool owned by the library (cached up to 1 GiB per device); under

@@ -387,7 +387,7 @@ struct interp {
 namespace {
 
 constexpr int kPsMaxKeys = 1024;           // keys: the pieces of the first c cosets, K^c <= 1024
-constexpr int64_t kPsChunk = 1 << 21;      // queries sorted at a time (the scratch stays near L2 size)
+constexpr int64_t kPsChunk = 1 << 22;      // queries sorted at a time (2^21 .. 2^23 measured: best value + grad)
 constexpr int kPsBlock = 4096;             // queries per CTA of the scatter
 
 // key of each query (mixed radix K over the pieces of its first c cosets) and the keys' totals
@@ -505,9 +505,9 @@ cudaError_t ps_pool(int dev, cudaMemPool_t *out)
 
 // whether a call of npts queries (at least 2^16) takes the pre-sort.  Measured on 2^24 random
 // queries, sort included: faster for many large pieces (K >= 8 pieces of >= 500 FMAs per coset:
-// BCC V_2, value 5.76 -> 3.19 ms, value+grad 6.95 -> 3.89 ms, adjoint 7.88 -> 3.57 ms) and for
-// the 8-coset D4 spline, whose gathers come from DRAM (value 19.3 -> 18.1 ms, value+grad
-// 19.7 -> 16.7 ms); slower for D4* (value 3.37 -> 3.91 ms: its 6 pieces' code is amortised
+// BCC V_2, value 5.76 -> 2.95 ms, value+grad 6.95 -> 3.61 ms, adjoint 7.88 -> 3.34 ms) and for
+// the 8-coset D4 spline, whose gathers come from DRAM (value 19.3 -> 17.7 ms, value+grad
+// 19.7 -> 16.6 ms); slower for D4* (value 3.37 -> 3.91 ms: its 6 pieces' code is amortised
 // within the tiles already, the sort is not) and no faster for BCC V_1 or FCC V_2, whose pieces
 // fit the instruction caches.  INTERP_B300_PRESORT=0 / 1 forces it off / on.
 bool presort_default(const SplineOps *ops)

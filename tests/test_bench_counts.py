@@ -1,5 +1,5 @@
 """Host logic of bench.py: the kernel launches a step claims (the evaluation kernel, the adjoint
-kernel plus the unpadding add, and with the piece pre-sort six kernels per chunk of 2^21 queries
+kernel plus the unpadding add, and with the piece pre-sort six kernels per chunk of 2^22 queries
 for the value forms, five plus the add for the adjoint) and when the pre-sort applies."""
 import os
 import sys
@@ -13,13 +13,13 @@ import bench  # noqa: E402
 
 
 def test_launches_per_step():
-    n = 1 << 24                                        # 8 chunks of 2^21
+    n = 1 << 24                                        # 4 chunks of 2^22
     assert bench.launches_per_step("value", n, False) == 1
     assert bench.launches_per_step("value_grad", n, False) == 1
     assert bench.launches_per_step("adjoint", n, False) == 2
-    assert bench.launches_per_step("value", n, True) == 48
-    assert bench.launches_per_step("value_grad", n + 1, True) == 54   # a ninth, ragged chunk
-    assert bench.launches_per_step("adjoint", n, True) == 41
+    assert bench.launches_per_step("value", n, True) == 24
+    assert bench.launches_per_step("value_grad", n + 1, True) == 30   # a fifth, ragged chunk
+    assert bench.launches_per_step("adjoint", n, True) == 21
 
 
 def test_presort_applies(monkeypatch):

@@ -1,6 +1,6 @@
 """GPU: the piece pre-sort.  For the splines where it measured faster (BCC V_2, the 8-coset D4)
 calls of 2^16 or more queries sort the queries on the device by the pieces of their first cosets
-(Sec. 4.3's sub-regions) before the piece-binned kernel, in chunks of 2^21, and return the
+(Sec. 4.3's sub-regions) before the piece-binned kernel, in chunks of 2^22, and return the
 results to the callers' positions.  A query's sum does not depend on its tile's other queries, so
 values, gradients and pullbacks equal the unsorted binned kernel's bit for bit; the adjoint's
 atomic scatter agrees within rounding; under stream capture the call runs unsorted.
@@ -14,8 +14,8 @@ from _gpu_common import VALUE_TOL, OracleSpline, grad_bound, make_interpolator, 
 
 pytestmark = pytest.mark.gpu
 
-# (grid sites per axis, queries): the BCC V_2 case spans two chunks of 2^21 plus a ragged tail
-CASES = {"bcc_voronoi2": (12, (1 << 21) + 4999), "d4s_8dir": (8, 70001), "d4_8dir": (6, 65537),
+# (grid sites per axis, queries): the BCC V_2 case spans two chunks of 2^22 plus a ragged tail
+CASES = {"bcc_voronoi2": (12, (1 << 22) + 4999), "d4s_8dir": (8, 70001), "d4_8dir": (6, 65537),
          "fcc_voronoi2": (10, 9001), "bcc_voronoi1": (12, 9007)}
 
 
