@@ -25,15 +25,15 @@
  *     (interp_backward) must not overlap other calls on the same handle.
  *   - Piece pre-sort: for splines where it measured faster (many large pieces, BCC V_2; the
  *     8-coset D4; interp_info_t.presort says which), eval, eval_grad and interp_backward calls
- *     of 2^16 or more queries first sort the queries
- *     on the device by the pieces (Sec. 4.3's sub-regions) of their first cosets, in chunks of
- *     2^22, so that the piece-binned kernel runs one piece's code for long stretches; results go
- *     back to the callers' positions.  Values and gradients are the same bits as without the
- *     sort.  The scratch (at most ~80 bytes per query of a chunk) comes per call from a
- *     stream-ordered memory pool owned by the library (cached up to 1 GiB per device); under
- *     stream capture, or when the pool has no room, the call runs without the sort.
- *     interp_backward_noalloc never sorts.  INTERP_B300_PRESORT=0 / 1 in the environment forces
- *     the sort off / on for any multi-piece spline and call size.
+ *     of 2^16 or more queries first sort the queries on the device by the pieces (Sec. 4.3's
+ *     sub-regions) of their first cosets, in chunks of 2^22, so that the piece-binned kernel
+ *     runs one piece's code for long stretches; results go back to the callers' positions.
+ *     Values, gradients and pullbacks are the same bits as without the sort; the adjoint's
+ *     atomic sums have no fixed order either way.  The scratch (at most ~80 bytes per query of
+ *     a chunk) comes per call from a stream-ordered memory pool owned by the library (cached up
+ *     to 1 GiB per device); under stream capture, or when the pool has no room, the call runs
+ *     without the sort.  interp_backward_noalloc never sorts.  INTERP_B300_PRESORT=0 / 1 in the
+ *     environment forces the sort off / on for any multi-piece spline and call size.
  */
 #ifndef INTERP_B300_H
 #define INTERP_B300_H
