@@ -8,7 +8,9 @@ not go through the oracle's own route (zonotope tiles, box-spline expansion):
 * partition of unity, reproduction of linear polynomials, and (V_2) the second-moment identity
   sum_n phi(x - n) n n^T = x x^T + (n+1) Cov(chi), with Cov(chi) integrated exactly over a
   tetrahedral decomposition of the Voronoi region;
-* two different tilings (two choices of generic heights) give the same V_n.
+* two different tilings (two choices of generic heights) give the same V_n;
+* V_2(x) pointwise against its definition chi * chi * chi: the 6-D volume of
+  {(y, w) : y, w, y + w - x in the Voronoi region}, from the region's half-spaces (qhull).
 """
 import numpy as np
 import pytest
@@ -203,3 +205,47 @@ def test_table1_voronoi_rows(golden_dir):
             if sum(b) < row["order"]:
                 assert np.ptp(m) < 1e-9, (row["name"], b)
         assert max(np.ptp(m) for b, m in moments.items() if sum(b) == row["order"]) > 1e-6, row["name"]
+
+
+def _vol6_triple_overlap(L, x):
+    """6-D volume of {(y, w) : y, w and y + w - x all in the Voronoi region}: with chi the indicator
+    of the region scaled by 1/|det L|, V_2 = chi * chi * chi gives
+    phi(x) = |det L| V_2(x) = vol / |det L|^2.  Half-spaces from the membership-derived relevant
+    vectors; interior point by linear programming (Chebyshev centre); volume by qhull in 6-D."""
+    from scipy.optimize import linprog
+    from scipy.spatial import ConvexHull, HalfspaceIntersection
+    V = _relevant_vectors(L)
+    b = (V * V).sum(axis=1) / 2
+    n = len(V)
+    A = np.zeros((3 * n, 6))
+    rhs = np.zeros(3 * n)
+    A[:n, :3], rhs[:n] = V, b
+    A[n:2 * n, 3:], rhs[n:2 * n] = V, b
+    A[2 * n:, :3], A[2 * n:, 3:], rhs[2 * n:] = V, V, b + V @ x
+    norms = np.linalg.norm(A, axis=1)
+    lp = linprog(np.r_[np.zeros(6), -1.0], A_ub=np.c_[A, norms], b_ub=rhs, bounds=[(None, None)] * 6 + [(0, None)])
+    if lp.status != 0 or lp.x[-1] < 1e-9:
+        return 0.0
+    pts = HalfspaceIntersection(np.c_[A, -rhs], lp.x[:6]).intersections
+    # the polytope is not simple (more than 6 facets meet at some vertices): qhull with its exact
+    # pre-merge and wide merges allowed; it agrees to rounding at most points, to ~1e-7 at a few
+    return ConvexHull(pts, qhull_options="Qx Q12").volume
+
+
+@pytest.mark.parametrize("lattice,npts", [("bcc", 5), ("fcc", 8)])
+def test_v2_is_the_triple_convolution_of_the_indicator(lattice, npts):
+    # pointwise pin of V_2 against its definition, independent of the oracle's tiling and
+    # box-spline expansion: phi(x) = vol{(y, w) : y, w, y + w - x in Vor} / |det L|^2
+    lat, gens, _ = _spec(f"{lattice}_voronoi2")
+    v = oracle.VoronoiSpline(lat.L, gens, 2)
+    det = abs(round(np.linalg.det(np.array(lat.L))))
+    rng = np.random.default_rng(17)
+    x = rng.uniform(-1.6, 1.6, (npts, 3))
+    x[0] = (0.0123, 0.0456, 0.0789)     # near the centre, off its symmetry planes (generic for qhull)
+    got = v.phi(x)
+    ref = np.array([_vol6_triple_overlap(lat.L, p) / det ** 2 for p in x])
+    assert np.all(ref > 0)
+    rel = np.abs(got - ref) / ref
+    # a dropped term or a wrong weight shows at 1e-3 or more; qhull's wide merges stay below 1e-6
+    assert rel.max() < 1e-6, rel
+    assert np.median(rel) < 1e-12, rel
