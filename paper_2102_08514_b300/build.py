@@ -124,6 +124,30 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False, job
     return OUT
 
 
+PEAKS_SRC = os.path.join(CSRC, "peaks.cu")
+PEAKS_OUT = os.path.join(BUILD, "libpeaks_b300.so")
+
+
+def build_peaks(force: bool = False) -> str:
+    """The microbenchmark library of csrc/peaks.cu (measured rooflines), rebuilt when its source
+    or the flags change."""
+    stamp = PEAKS_OUT + ".stamp"
+    h = hashlib.sha256(" ".join(NVCC_FLAGS).encode())
+    with open(PEAKS_SRC, "rb") as f:
+        h.update(f.read())
+    digest = h.hexdigest()
+    if not force and os.path.exists(PEAKS_OUT) and os.path.exists(stamp) and open(stamp).read().strip() == digest:
+        return PEAKS_OUT
+    os.makedirs(BUILD, exist_ok=True)
+    tmp = PEAKS_OUT + f".tmp{os.getpid()}"
+    subprocess.check_call([nvcc(), *NVCC_FLAGS, "-shared", "-o", tmp, PEAKS_SRC])
+    os.replace(tmp, PEAKS_OUT)
+    with open(stamp, "w") as f:
+        f.write(digest)
+    return PEAKS_OUT
+
+
 if __name__ == "__main__":
+    build_peaks(force="--force" in sys.argv)
     print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv or "--ptxas-v" in sys.argv,
                 ptxas_v="--ptxas-v" in sys.argv))

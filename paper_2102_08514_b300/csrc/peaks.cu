@@ -1,0 +1,163 @@
+// peaks.cu -- microbenchmarks of the B300 resources the evaluator's kernels are bound by.
+//
+// The rooflines of the evaluator divide by these measured rates, not by spec-sheet products:
+//   * FP32 FMA throughput (the bound of ray-coherent and spatially sorted queries, whose
+//     coefficient gathers hit L1);
+//   * L2-resident read bandwidth (coalesced 16-byte loads over a buffer that fits L2);
+//   * random gather rates: loads of 4, 16 or 32 bytes at pseudo-random addresses, each inside
+//     one 32-byte sector, from an L2-resident buffer (every load its own L1 miss and L1 -> L2
+//     request: the access pattern of the coefficient gathers of random queries) and from an
+//     L1-resident one (every load a hit: the L1 lookup rate of divergent loads);
+//   * L2 atomic throughput: red.global.add.f32 at pseudo-random addresses of an L2-resident
+//     buffer (the scatter of the adjoint).
+// Each entry point launches one kernel on the caller's stream; the caller times it with CUDA
+// events and converts with the work counts documented beside each entry point.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace {
+
+// FMA chains: NCH independent accumulators per thread, ITER rounds of NCH FMAs each
+constexpr int kFmaChains = 8;
+constexpr int kFmaUnroll = 64;
+
+__global__ void __launch_bounds__(256) k_fma(float *out, int iters, float a, float b)
+{
+    float acc[kFmaChains];
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c) acc[c] = (float)(threadIdx.x + c);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < kFmaUnroll; ++u) {
+#pragma unroll
+            for (int c = 0; c < kFmaChains; ++c) acc[c] = fmaf(acc[c], a, b);
+        }
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c) s += acc[c];
+    // never true for the arguments the runner passes; keeps the chains live
+    if (s == 1234.5f) out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// coalesced float4 reads of an L2-resident buffer, `passes` times over
+__global__ void __launch_bounds__(256) k_l2_read(const float4 *__restrict__ buf, int64_t n4, int passes,
+                                                 float *__restrict__ out)
+{
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int p = 0; p < passes; ++p) {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+            const float4 v = __ldcg(buf + i);
+            acc.x += v.x;
+            acc.y += v.y;
+            acc.z += v.z;
+            acc.w += v.w;
+        }
+    }
+    const float s = acc.x + acc.y + acc.z + acc.w;
+    if (s == 1234.5f) out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// pseudo-random word index in [0, mask]: one multiply-add per step of a 32-bit LCG
+__device__ __forceinline__ uint32_t lcg(uint32_t x) { return x * 1664525u + 1013904223u; }
+
+// one W-float load at element offset i of buf (W = 1, 4 or 8; 8 is one 32-byte sector)
+template <int W>
+__device__ __forceinline__ float load_w(const float *__restrict__ buf, uint32_t i)
+{
+    if constexpr (W == 1) {
+        return __ldg(buf + i);
+    } else if constexpr (W == 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(buf) + i);
+        return (v.x + v.y) + (v.z + v.w);
+    } else {
+        float a[8];
+        asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=f"(a[0]), "=f"(a[1]), "=f"(a[2]), "=f"(a[3]), "=f"(a[4]), "=f"(a[5]), "=f"(a[6]), "=f"(a[7])
+                     : "l"(buf + 8 * (size_t)i));
+        return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    }
+}
+
+// each thread: `iters` rounds of 8 independent W-float loads at pseudo-random W-aligned addresses
+// (each inside one 32-byte sector); the buffer holds mask + 1 W-vectors (a power of two)
+template <int W>
+__global__ void __launch_bounds__(128) k_gather(const float *__restrict__ buf, uint32_t mask, int iters,
+                                                float *__restrict__ out)
+{
+    uint32_t st[8];
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) st[u] = lcg(t * 8u + (uint32_t)u + 0x9e3779b9u);
+    float acc = 0.0f;
+    for (int i = 0; i < iters; ++i) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            st[u] = lcg(st[u]);
+            v[u] = load_w<W>(buf, (st[u] >> 4) & mask);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += v[u];
+    }
+    if (acc == 1234.5f) out[t] = acc;
+}
+
+// each thread: `iters` rounds of 4 red.global.add.f32 at pseudo-random word addresses
+__global__ void __launch_bounds__(128) k_red(float *__restrict__ buf, uint32_t mask, int iters)
+{
+    uint32_t st[4];
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) st[u] = lcg(t * 4u + (uint32_t)u + 0x7f4a7c15u);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            st[u] = lcg(st[u]);
+            atomicAdd(buf + ((st[u] >> 4) & mask), 1.0f);
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+// FP32 FMA: grid x 256 threads, each 8 chains x 64 x iters FMAs (2 FLOP each).
+// FLOP = grid * 256 * 8 * 64 * iters * 2.  `out` (grid * 256 floats) is never written.
+int peaks_fma(int grid, int iters, float *out, void *stream)
+{
+    k_fma<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(out, iters, 0.999999f, 1e-7f);
+    return (int)cudaPeekAtLastError();
+}
+
+// L2-resident read: bytes = n4 * 16 * passes.  `out` (grid * 256 floats) is never written.
+int peaks_l2_read(const void *buf, int64_t n4, int passes, int grid, float *out, void *stream)
+{
+    k_l2_read<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const float4 *>(buf), n4, passes,
+                                                                     out);
+    return (int)cudaPeekAtLastError();
+}
+
+// random gather: loads = grid * 128 * 8 * iters, each of `width` floats (1, 4 or 8) inside one
+// 32-byte sector; buf holds (mask + 1) * width floats (mask + 1 a power of two) and is 32-byte
+// aligned.  `out` (grid * 128 floats) is never written.
+int peaks_gather(const float *buf, uint32_t mask, int width, int grid, int iters, float *out, void *stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (width == 1) k_gather<1><<<grid, 128, 0, st>>>(buf, mask, iters, out);
+    else if (width == 4) k_gather<4><<<grid, 128, 0, st>>>(buf, mask, iters, out);
+    else if (width == 8) k_gather<8><<<grid, 128, 0, st>>>(buf, mask, iters, out);
+    else return (int)cudaErrorInvalidValue;
+    return (int)cudaPeekAtLastError();
+}
+
+// random L2 atomics: red.add.f32 count = grid * 128 * 4 * iters into buf (mask + 1 floats)
+int peaks_red(float *buf, uint32_t mask, int grid, int iters, void *stream)
+{
+    k_red<<<grid, 128, 0, static_cast<cudaStream_t>(stream)>>>(buf, mask, iters);
+    return (int)cudaPeekAtLastError();
+}
+
+}  // extern "C"
