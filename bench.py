@@ -41,9 +41,6 @@ METRIC = "evals/s (value+grad, FP32, <=2e-6 rel err)"
 DEFAULT_FORM = {"bcc_linear_16": "value", "bcc_quintic_128": "value_grad", "fcc_6dir_128": "value_grad",
                 "cc_7dir_256": "value", "d4s_8dir_48": "value"}
 UNIT = "evals/s"
-SM_COUNT = 148
-FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2032.0
 
 
 def peaks():
@@ -51,7 +48,7 @@ def peaks():
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f), "measured"
     except OSError:
-        return {"hbm_gbs": 6400.0, "sm_max_mhz": SM_MAX_MHZ}, "fallback"
+        return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
 
 
 def presort_applies(info, n: int) -> bool:
@@ -75,9 +72,68 @@ def launches_per_step(form: str, n: int, presort: bool) -> int:
     return 6 * chunks if presort else 1
 
 
-def fp32_peak_tflops():
-    # derived: SMs x FP32 lanes x 2 FLOP per FMA x max SM clock
-    return SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+_PEAKS = {}
+
+
+def measured_peaks(torch):
+    """The rooflines' denominators, measured on this GPU in this run by the microbenchmarks of
+    paper_2102_08514_b300/peaks.py (FP32 FMA rate, random-gather sector rate, L2 atomic rate, L2
+    read bandwidth), with the SM clock sampled while they ran.  Measured once per process."""
+    if not _PEAKS:
+        from paper_2102_08514_b300 import peaks as pk
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            res = pk.measure(torch)
+        res["clocks"] = clk.summary()
+        _PEAKS.update(res)
+    return _PEAKS
+
+
+def brick_lb(s, esz, M, a):
+    """log2 brick width of axis a of the library's coefficient layout (csrc/layout.h, cosets in
+    separate arrays): the brick's 32-byte address bits dealt one per axis from axis 0."""
+    bits, lb, i = (32 // esz).bit_length() - 1, 0, 0
+    while bits > 0:
+        if i == a:
+            lb += 1
+        i, bits = (i + 1) % s, bits - 1
+    return lb
+
+
+def distinct_sectors_per_query(spline: str, pts, esz: int = 4):
+    """Mean number of distinct 32-byte sectors (bricks) a query's coefficient gathers touch: the
+    gather work of one query in the library's bricked layout, which bounds random queries (each
+    distinct sector is one L1 miss and one L1 -> L2 request).  One-piece 3-D splines only (the
+    stencil is then the same for every folded point); None otherwise.  Follows the kernels'
+    steps: nearest coset site, |y| sorted descending (signed permutation), the piece's stencil."""
+    import json as _json
+    with open(os.path.join(ROOT, "paper_2102_08514_b300", "csrc", "generated", "splines.json")) as f:
+        meta = _json.load(f)["splines"][spline]
+    if meta["s"] != 3 or len(meta["pieces"]) != 1:
+        return None
+    D, H, cosets = meta["D"], meta["halo"], np.asarray(meta["cosets"])
+    site = np.asarray(meta["pieces"][0]["sites"])
+    M = len(cosets)
+    lbs = [brick_lb(3, esz, M, a) for a in range(3)]
+    x = np.asarray(pts, dtype=np.float64)
+    n = len(x)
+    keys = []
+    for k, l in enumerate(cosets):
+        u = x - l
+        i = np.floor(u / D + 0.5).astype(np.int64)
+        y = u - D * i
+        sg = np.where(y < 0, -1, 1)
+        order = np.argsort(-np.abs(y), axis=1, kind="stable")
+        P = np.repeat((i + 2 * H)[:, None, :], len(site), axis=1)
+        rows = np.arange(n)
+        for A in range(3):
+            ax = order[:, A]
+            P[rows, :, ax] += (sg[rows, ax][:, None] * site[None, :, A])
+        b = np.zeros(P.shape[:2], dtype=np.int64)
+        for a in range(3):
+            b = b * 4096 + (P[..., a] >> lbs[a])
+        keys.append(b + (k << 40))
+    K = np.sort(np.concatenate(keys, axis=1), axis=1)
+    return float((1 + (np.diff(K, axis=1) != 0).sum(axis=1)).mean())
 
 
 def workload_description(wl, form="value_grad", storage="f32"):
@@ -222,7 +278,8 @@ def run_batch(args):
         total_ms, per = time_steps(torch, batch.run, args.steps, args.warmup, stream, lambda: None)
     ms = total_ms / args.steps
     achieved = flops / (ms * 1e-3) / 1e12
-    peak = fp32_peak_tflops()
+    pk = measured_peaks(torch)
+    peak = pk["fp32_tflops"]
     line = {
         "metric": "evals/s (batched value, FP32)", "value": total_q / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -233,7 +290,8 @@ def run_batch(args):
                    "queries": total_q, "tiles": tiles},
         "gpu_launches": 2 * args.steps, "clocks": clk.summary(),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_batch (3-D and 4-D)"},
+                     "traffic": None, "kernel": "k_batch (3-D and 4-D)",
+                     "peak_note": "FP32 FMA rate measured in this run (peaks_fma microbenchmark), of measured"},
     }
     print(json.dumps(line), flush=True)
 
@@ -483,9 +541,12 @@ def run_ours(args):
     flops_per_launch = 2.0 * fma * n
     kern_ms = statistics.mean(per)
     achieved = flops_per_launch / (kern_ms * 1e-3) / 1e12
-    peak = fp32_peak_tflops()
+    pk = measured_peaks(torch)
+    peak = pk["fp32_tflops"]
     kname = f"k_eval<{wl.spline},{args.storage},{form}>" if form != "adjoint" else f"k_adjoint<{wl.spline}>"
     traffic, l1l2_frac = recorded_capture(kname)
+    esz = 4 if args.storage == "f32" else 2
+    sectors = distinct_sectors_per_query(wl.spline, pts_h[:1 << 16], esz) if form != "adjoint" else None
     presort = presort_applies(info, n)
     if presort:
         kname += " after the piece pre-sort (whole call timed)"
@@ -520,12 +581,23 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": kname,
                      "flops_per_query": 2.0 * fma,
-                     "peak_note": "FP32 FMA peak derived: 148 SMs x 128 lanes x 2 FLOP x 2032 MHz (of derived)",
-                     # random queries are bound by the gather's L1 -> L2 miss requests, not the
-                     # FP32 pipe: that path's fraction of its peak, from the kernel's ncu capture
-                     "binding_resource": {"name": "L1 -> L2 miss requests (l1tex__m_l1tex2xbar_req_cycles_active)",
-                                          "frac_of_peak": l1l2_frac,
-                                          "source": "ncu capture, profiles/k_eval_bcc_quintic_value_grad.md"}},
+                     "flops_note": "FP32 operations of the method per query (generator count: nonzeros of A_j plus "
+                                   "the Horner steps on structurally nonzero data, summed over the cosets), 2 FLOP each",
+                     "peak_note": f"FP32 FMA rate measured in this run (peaks_fma microbenchmark, "
+                                  f"{pk['sms']} SMs, SM clock {pk['clocks']['sm_mhz']} MHz), of measured",
+                     # random queries are bound by the coefficient gathers in L1TEX, not the FP32
+                     # pipe: the distinct sectors a query touches against the measured rate of
+                     # random sector gathers (one L1 miss request each)
+                     "binding_resource": {
+                         "name": "coefficient gathers: distinct 32-byte sectors per query (L1 miss requests)",
+                         "sectors_per_query": sectors,
+                         "achieved_gsectors_s": sectors * n / (kern_ms * 1e-3) / 1e9 if sectors else None,
+                         "peak_gsectors_s": pk["gather_gsectors_s"],
+                         "frac": sectors * n / (kern_ms * 1e-3) / 1e9 / pk["gather_gsectors_s"] if sectors else None,
+                         "peak_note": "random 4-byte gathers from a 16 MiB L2-resident buffer, measured in this run",
+                         "ncu_l1_to_l2_request_cycles_frac": l1l2_frac}},
+        "peaks": {k: pk[k] for k in ("sms", "fp32_tflops", "gather_gsectors_s", "gather4B_l1_gloads_s",
+                                     "red_gatomics_s", "l2_read_gbs", "clocks")},
         "forms": {k: {"evals_per_s": (RAY_EVALS[0] if k.startswith("rays") else n) / (v * 1e-3), "ms": v}
                   for k, v in form_ms.items()},
     }
@@ -539,9 +611,17 @@ def run_ours(args):
         if k in form_ms:
             fma_s = info.fma_value_per_query if k == "rays_value" else info.fma_grad_per_query
             line["forms"][k]["tflops"] = 2.0 * fma_s * RAY_EVALS[0] / (form_ms[k] * 1e-3) / 1e12
-    for k in ("value", "value_grad", "rays_value", "rays_value_grad"):
+    if "value_sorted" in form_ms:
+        line["forms"]["value_sorted"]["tflops"] = 2.0 * info.fma_value_per_query * n / (form_ms["value_sorted"] * 1e-3) / 1e12
+    for k in ("value", "value_grad", "value_sorted", "rays_value", "rays_value_grad"):
         if k in line["forms"] and "tflops" in line["forms"][k]:
             line["forms"][k]["frac_of_fp32_peak"] = line["forms"][k]["tflops"] / peak
+    # the adjoint's contributions (query, site) against the measured rate of random L2 atomics
+    # (the bound of a scatter with one global atomic per contribution)
+    contrib = info.lookups_per_query * n
+    line["forms"]["adjoint"]["contributions_per_s"] = contrib / (form_ms["adjoint"] * 1e-3)
+    line["forms"]["adjoint"]["over_l2_atomic_peak"] = contrib / (form_ms["adjoint"] * 1e-3) / (pk["red_gatomics_s"] * 1e9)
+    line["forms"]["adjoint"]["over_value"] = form_ms["adjoint"] / form_ms["value"]
     if args.workload != WORKLOAD or args.storage != "f32" or form != DEFAULT_FORM[WORKLOAD] or args.spline:
         line["metric"] = f"evals/s ({form}, {args.storage} storage)"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -32,8 +32,12 @@
  *     atomic sums have no fixed order either way.  The scratch (at most ~80 bytes per query of
  *     a chunk) comes per call from a stream-ordered memory pool owned by the library (cached up
  *     to 1 GiB per device); under stream capture, or when the pool has no room, the call runs
- *     without the sort.  interp_backward_noalloc never sorts.  INTERP_B300_PRESORT=0 / 1 in the
- *     environment forces the sort off / on for any multi-piece spline and call size.
+ *     without the sort.  interp_backward_noalloc never sorts.  The handle's "presort" option
+ *     (interp_set_option) forces the sort off / on for any multi-piece spline and call size.
+ *   - Launch options are per handle (interp_set_option).  Their initial values are read from the
+ *     environment once, when the handle is created: INTERP_B300_BINNED, INTERP_B300_PRESORT,
+ *     INTERP_B300_DENSE, INTERP_B300_ADJOINT_BINS (0 / 1) and INTERP_B300_BINCFG (=small); later changes of the
+ *     environment do not affect existing handles.
  */
 #ifndef INTERP_B300_H
 #define INTERP_B300_H
@@ -71,6 +75,11 @@ const char *interp_strerror(interp_status st);
 int interp_num_splines(void);
 const char *interp_spline_name(int i);
 const char *interp_table_digest(void);
+
+/* Number of device allocation calls (cudaMalloc, cudaMallocAsync, cudaMallocFromPoolAsync and
+ * cudaMemPoolCreate) the library has made in this process so far, over all handles and devices.
+ * For checking that an entry point allocates nothing (interp_backward_noalloc). Not in the paper. */
+long long interp_debug_device_allocations(void);
 
 /*
  * interp_create -- build a handle for the lattice L Z^s (L: s x s integer, row-major, full rank)
@@ -123,6 +132,25 @@ typedef struct {
                                   /*    default (see the conventions above)                 */
 } interp_info_t;
 interp_status interp_info(const interp_t *h, interp_info_t *info);
+
+/*
+ * interp_set_option / interp_get_option -- per-handle launch options (not in the paper; they
+ * select among equivalent kernels, results are the same bits except where noted):
+ *   "binned"           -1 default (piece-binned kernels for splines with >= 4 pieces), 0 plain
+ *                      kernels, 1 piece-binned kernels for any multi-piece spline
+ *   "presort"          -1 default (see the piece pre-sort above), 0 never, 1 every call of a
+ *                      multi-piece spline (adjoint sums change order, see interp_backward)
+ *   "dense"            -1 default (dense piece tables for the rays of the splines that have
+ *                      them), 0 never, 1 also for the binned evaluation
+ *   "bin_small_tiles"  0 default, 1 binned kernels on 256-query tiles of 128-thread CTAs
+ *   "adjoint_bins"     -1 default (interp_backward sorts many queries into spatial bins first,
+ *                      see there), 0 never, 1 always where the spline allows it
+ * Options take effect for calls enqueued after the change; do not change them while another
+ * thread enqueues calls on the handle.  Errors: EINVAL (null pointer, unknown name, value out of
+ * range).
+ */
+interp_status interp_set_option(interp_t *h, const char *name, int value);
+interp_status interp_get_option(const interp_t *h, const char *name, int *value);
 
 /*
  * interp_set_coeffs -- copy the coefficients into the handle, converting to the storage type.
@@ -187,10 +215,18 @@ interp_status interp_eval_host(interp_t *h, const float *pts, int64_t npts, floa
  * dcoeffs has the coefficient layout of interp_set_coeffs (FP32) and is ACCUMULATED into: zero it
  * first for a plain gradient.  The scatter uses FP32 atomics into a handle-owned padded buffer,
  * so the order of additions, and the last bits of dcoeffs, vary between runs.  dcoeffs may be
- * NULL to compute dpts only.  3-D splines: each block of 1024 consecutive queries whose cells fit
- * a small box (e.g. after interp_sort_points) is summed in shared memory first, with one global
- * atomic per touched coefficient; other blocks (and 4-D splines) add every contribution with its
- * own atomic.
+ * NULL to compute dpts only.
+ *   - 3-D splines with fewer than 4 pieces, calls with many queries (the contributions outnumber
+ *     the shared-memory boxes' sites about twice; option "adjoint_bins" = 0 / 1 forces it off /
+ *     on): the queries are first counting-sorted on the device into spatial bins of 16^3 (8^3 for
+ *     FCC) coset cells; each bin's contributions are summed in a shared-memory box and added to
+ *     the padded buffer once per site.  The scratch (16 bytes per query plus 16 per bin) comes
+ *     from the library's stream-ordered pool (see the piece pre-sort); under stream capture, or
+ *     when the pool has no room, the call takes the path below.
+ *   - Otherwise, 3-D splines: each block of 1024 consecutive queries whose cells fit a small box
+ *     (e.g. after interp_sort_points) is summed in shared memory first, with one global atomic per
+ *     touched coefficient; other blocks (and 4-D splines) add every contribution with its own
+ *     atomic.
  */
 interp_status interp_backward(interp_t *h, const float *pts, int64_t npts, const float *gout, float *dcoeffs,
                               float *dpts, void *stream);
@@ -238,8 +274,11 @@ void interp_batch_destroy(interp_batch_t *b);
  * loads this library holds until the process exits.  The caller still passes all inputs and
  * outputs (same arguments and semantics as interp_backward).
  *
- *   - Limit: n_cosets * (elements of one padded FP32 coset array) must not exceed
- *     INTERP_NOALLOC_MAX_GRAD_ELEMS, else INTERP_ESIZE is returned and nothing runs.
+ *   - Limit: when dcoeffs is not NULL, n_cosets * (elements of one padded FP32 coset array) must
+ *     not exceed INTERP_NOALLOC_MAX_GRAD_ELEMS, else INTERP_ESIZE is returned and nothing runs.
+ *     A dpts-only call (dcoeffs == NULL) does not use the array and has no such limit.
+ *   - dpts is computed without the piece pre-sort (whose scratch comes from a memory pool), so
+ *     no call allocates, whatever the spline and the number of queries.
  *   - The first call on a device (with that device current, which must be the handle's device)
  *     looks up the array's device address once; make that first call before any stream capture.
  *   - All calls share the one array and it keeps the previous call's contents; each call clears

@@ -65,11 +65,15 @@ def load(path: str = LIB_PATH):
     lib.interp_spline_name.argtypes = [I]
     lib.interp_spline_name.restype = ctypes.c_char_p
     lib.interp_table_digest.restype = ctypes.c_char_p
+    lib.interp_debug_device_allocations.argtypes = []
+    lib.interp_debug_device_allocations.restype = ctypes.c_longlong
     lib.interp_create.argtypes = [I, P, P, I, P, I, ctypes.POINTER(ctypes.c_void_p)]
     lib.interp_create_named.argtypes = [ctypes.c_char_p, P, I, ctypes.POINTER(ctypes.c_void_p)]
     lib.interp_destroy.argtypes = [P]
     lib.interp_destroy.restype = None
     lib.interp_info.argtypes = [P, ctypes.POINTER(InterpInfo)]
+    lib.interp_set_option.argtypes = [P, ctypes.c_char_p, I]
+    lib.interp_get_option.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]
     lib.interp_set_coeffs.argtypes = [P, P, I, I, P]
     lib.interp_prefilter.argtypes = [P, P, I, P, P, P]
     lib.interp_eval.argtypes = [P, P, I64, P, P]
@@ -93,7 +97,7 @@ def load(path: str = LIB_PATH):
     for f in (lib.interp_batch_create, lib.interp_batch_autotune, lib.interp_batch_tile, lib.interp_batch_set_tile,
               lib.interp_batch_run):
         f.restype = I
-    for f in (lib.interp_create, lib.interp_create_named, lib.interp_info, lib.interp_prefilter, lib.interp_set_coeffs, lib.interp_eval, lib.interp_eval_grad,
+    for f in (lib.interp_set_option, lib.interp_get_option, lib.interp_create, lib.interp_create_named, lib.interp_info, lib.interp_prefilter, lib.interp_set_coeffs, lib.interp_eval, lib.interp_eval_grad,
               lib.interp_backward, lib.interp_debug_indices, lib.interp_backward_noalloc):
         f.restype = I
     _lib = lib
@@ -102,7 +106,9 @@ def load(path: str = LIB_PATH):
 
 def exported_symbols() -> list[str]:
     return ["interp_strerror", "interp_num_splines", "interp_spline_name", "interp_table_digest",
-            "interp_create", "interp_create_named", "interp_destroy", "interp_prefilter", "interp_info", "interp_set_coeffs", "interp_eval",
+            "interp_debug_device_allocations",
+            "interp_create", "interp_create_named", "interp_destroy", "interp_prefilter", "interp_info",
+            "interp_set_option", "interp_get_option", "interp_set_coeffs", "interp_eval",
             "interp_eval_grad", "interp_backward", "interp_debug_indices", "interp_backward_noalloc",
             "interp_batch_create", "interp_batch_autotune", "interp_batch_tile", "interp_batch_set_tile",
             "interp_batch_run", "interp_batch_destroy", "interp_eval_rays", "interp_eval_host",
@@ -149,6 +155,11 @@ def table_digest() -> str:
     return load().interp_table_digest().decode()
 
 
+def interp_debug_device_allocations() -> int:
+    """Device allocation calls the library has made in this process so far."""
+    return int(load().interp_debug_device_allocations())
+
+
 # ----------------------------------------------------------------------------- C-named wrappers
 
 def interp_create_named(name: str, dims, storage: int = INTERP_F32):
@@ -182,6 +193,17 @@ def interp_info(h) -> InterpInfo:
     info = InterpInfo()
     _check(load().interp_info(h, ctypes.byref(info)), "interp_info")
     return info
+
+
+def interp_set_option(h, name: str, value: int):
+    """Per-handle launch option ("binned", "presort", "dense", "bin_small_tiles"; see the C header)."""
+    _check(load().interp_set_option(h, name.encode(), int(value)), "interp_set_option")
+
+
+def interp_get_option(h, name: str) -> int:
+    v = ctypes.c_int()
+    _check(load().interp_get_option(h, name.encode(), ctypes.byref(v)), "interp_get_option")
+    return v.value
 
 
 def interp_set_coeffs(h, coeffs, stream=None):
@@ -429,6 +451,12 @@ class Interpolator:
         if tuple(coeffs.shape) != self.shape:
             raise ValueError(f"coefficients must have shape {self.shape}, got {tuple(coeffs.shape)}")
         interp_set_coeffs(self._h, coeffs, stream)
+
+    def set_option(self, name: str, value: int):
+        interp_set_option(self._h, name, value)
+
+    def get_option(self, name: str) -> int:
+        return interp_get_option(self._h, name)
 
     def prefilter(self, samples, taps, weights, stream=None):
         """Coefficients from samples by a lattice filter (interp_prefilter)."""

@@ -6,6 +6,7 @@
 #include "interp.h"
 
 #include <algorithm>
+#include <atomic>
 #include <array>
 #include <cstdlib>
 #include <cstring>
@@ -21,6 +22,7 @@
 
 #include "generated/splines.h"
 
+#include "kernels.cuh"
 #include "registry.h"
 
 INTERP_GEN_SPLINES(INTERP_FILL_DECL)
@@ -318,6 +320,24 @@ interp_status cuda_status(cudaError_t e)
     return INTERP_ECUDA;
 }
 
+// every device allocation call of the library goes through these (counted for
+// interp_debug_device_allocations)
+std::atomic<long long> g_dev_allocs{0};
+
+template <class T>
+cudaError_t lib_malloc(T **p, size_t bytes)
+{
+    g_dev_allocs.fetch_add(1, std::memory_order_relaxed);
+    return cudaMalloc(reinterpret_cast<void **>(p), bytes);
+}
+
+template <class T>
+cudaError_t lib_malloc_async(T **p, size_t bytes, cudaStream_t st)
+{
+    g_dev_allocs.fetch_add(1, std::memory_order_relaxed);
+    return cudaMallocAsync(reinterpret_cast<void **>(p), bytes, st);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------------ the handle
@@ -362,6 +382,14 @@ struct interp {
     void *coeffs = nullptr;    // padded, bricked storage
     float *dpad = nullptr;     // padded FP32 gradient buffer (allocated by the first interp_backward)
     int device = 0;
+    int sms = 148;                  // SMs of the handle's device (grid caps)
+    // launch options (interp_set_option; initial values from the environment at creation):
+    // -1 = the measured default
+    int opt_binned = -1;            // piece-binned kernels for multi-piece splines: 0 / 1
+    int opt_presort = -1;           // the piece pre-sort: 0 / 1 for any multi-piece spline and call size
+    int opt_bin_small = 0;          // binned kernels on 256-query tiles: 0 / 1
+    int opt_dense = -1;             // dense piece tables: 0 / 1
+    int opt_adjoint_bins = -1;      // the adjoint on spatially binned queries: 0 / 1
     unsigned *sort_keys = nullptr;  // interp_sort_points bin counters
     int sort_nkeys = 0;
     // interp_eval_host staging: kHostSlots slots of (points, values, gradients), one stream each
@@ -489,6 +517,7 @@ cudaError_t ps_pool(int dev, cudaMemPool_t *out)
         p.location.type = cudaMemLocationTypeDevice;
         p.location.id = dev;
         cudaMemPool_t pool = nullptr;
+        g_dev_allocs.fetch_add(1, std::memory_order_relaxed);
         cudaError_t e = cudaMemPoolCreate(&pool, &p);
         if (e != cudaSuccess) return e;
         uint64_t keep = 1ull << 30;
@@ -515,11 +544,22 @@ bool presort_default(const SplineOps *ops)
     return (ops->K >= 8 && ops->fma_value / ops->M >= 500.0) || (ops->M >= 8 && ops->K >= 4);
 }
 
-bool presort_wanted(const SplineOps *ops, int64_t npts)
+bool presort_wanted(const interp *h, int64_t npts)
 {
-    const char *e = std::getenv("INTERP_B300_PRESORT");
-    if (e) return e[0] == '1';
-    return npts >= (1 << 16) && presort_default(ops);
+    if (h->opt_presort >= 0) return h->opt_presort == 1;
+    return npts >= (1 << 16) && presort_default(h->ops);
+}
+
+// the handle's launch options as the launchers' flags
+int launch_flags(const interp *h)
+{
+    int f = 0;
+    if (h->opt_bin_small == 1) f |= ibr::FLAG_BIN_SMALL;
+    if (h->opt_dense == 1) f |= ibr::FLAG_DENSE_ON;
+    if (h->opt_dense == 0) f |= ibr::FLAG_DENSE_OFF;
+    if (h->opt_binned == 1) f |= ibr::FLAG_BINNED_ON;
+    if (h->opt_binned == 0) f |= ibr::FLAG_BINNED_OFF;
+    return f;
 }
 
 struct PresortWs {
@@ -554,20 +594,21 @@ cudaError_t ps_unpermute(int s, const PresortWs &w, int m, float *out, float *gr
 
 }  // namespace
 
+// allow_presort = false: never the piece pre-sort (it takes scratch from the library's pool)
 static cudaError_t eval_launch(const interp *h, const float *pts, int64_t npts, float *out, float *grad, const float *gout,
-                        int mode, cudaStream_t st)
+                               int mode, cudaStream_t st, bool allow_presort = true)
 {
     const int dt = h->storage == INTERP_F32 ? 0 : (h->storage == INTERP_F16 ? 1 : 2);
     // splines with many pieces (D4*: 6) run the piece-binned kernel; with few small pieces (FCC: 3)
-    // the sort costs more than the divergence it removes (measured).  INTERP_B300_BINNED=0 / 1
-    // forces the plain / binned kernel.
-    const char *bn = std::getenv("INTERP_B300_BINNED");
-    const bool want = bn ? bn[0] == '1' : h->ops->K >= 4;
+    // the sort costs more than the divergence it removes (measured).  The handle's "binned"
+    // option forces the plain / binned kernel.
+    const bool want = h->opt_binned >= 0 ? h->opt_binned == 1 : h->ops->K >= 4;
     const bool binned = want && h->ops->eval_binned[dt][mode];
     const ibr::EvalFn fn = (binned ? h->ops->eval_binned : h->ops->eval)[dt][mode];
+    const int flags = launch_flags(h);
     PresortWs w;
-    if (!binned || !presort_wanted(h->ops, npts) || !ps_acquire(h, npts, st, w))
-        return fn(pts, npts, h->coeffs, h->lay, out, grad, gout, st);
+    if (!binned || !allow_presort || !presort_wanted(h, npts) || !ps_acquire(h, npts, st, w))
+        return fn(pts, npts, h->coeffs, h->lay, out, grad, gout, flags, st);
     const int s = h->s;
     cudaError_t e = cudaSuccess;
     for (int64_t q0 = 0; q0 < npts && e == cudaSuccess; q0 += kPsChunk) {
@@ -576,7 +617,7 @@ static cudaError_t eval_launch(const interp *h, const float *pts, int64_t npts, 
         // value (and gradient) of the sorted queries; the pullback (mode 2) writes w * grad only
         if (e == cudaSuccess)
             e = fn(w.pts_s, m, h->coeffs, h->lay, mode == 2 ? nullptr : w.out_s, mode >= 1 ? w.grad_s : nullptr,
-                   mode == 2 ? w.gout_s : nullptr, st);
+                   mode == 2 ? w.gout_s : nullptr, flags, st);
         if (e == cudaSuccess)
             e = ps_unpermute(s, w, m, mode == 2 || !out ? nullptr : out + q0, mode >= 1 ? grad + q0 * s : nullptr, st);
     }
@@ -584,12 +625,215 @@ static cudaError_t eval_launch(const interp *h, const float *pts, int64_t npts, 
     return e;
 }
 
-// dL/dc into h->dpad; multi-piece splines with large pieces take the pre-sort like eval_launch
-// (the adjoint's atomic scatter has no fixed summation order either way)
+// ------------------------------------------------------------------------------------ adjoint on spatial bins
+//
+// interp_backward on many queries of a 3-D spline with few pieces: a counting sort of the queries
+// into bins of 2^box_lb coset-0 cells per axis (count, scan, scatter of (x, y, z, gout) records),
+// then one work item per chunk of a bin, which sums its contributions in a shared-memory box and
+// adds the box to the padded gradient buffer (ib::k_adjoint_box).  The scratch comes per call from
+// the library's stream-ordered pool, as for the piece pre-sort.
+
+namespace {
+
+constexpr int kBoxChunk = 32768;          // queries per work item at most
+constexpr int kBoxSharedBins = 4096;      // per-CTA bin counters in shared memory up to this many bins
+constexpr int kBoxBlock = 4096;           // queries per CTA of the count and scatter kernels
+
+struct BoxGeom {
+    int D, H2, lb, nb[3], nbins;
+};
+
+__device__ __forceinline__ int box_key(const float *p, float w, const BoxGeom &g, const ibl::Layout &L)
+{
+    const float x[3] = {p[0], p[1], p[2]};
+    return g.D == 2 ? ib::box_key3<2>(x, w, g.H2, L, g.lb, g.nb) : ib::box_key3<1>(x, w, g.H2, L, g.lb, g.nb);
+}
+
+__global__ void __launch_bounds__(256) k_box_count(const float *__restrict__ pts, const float *__restrict__ gout, int n,
+                                                   BoxGeom g, ibl::Layout L, unsigned *__restrict__ counts)
+{
+    __shared__ unsigned hist[kBoxSharedBins];
+    const bool sh = g.nbins <= kBoxSharedBins;
+    if (sh) {
+        for (int i = threadIdx.x; i < g.nbins; i += blockDim.x) hist[i] = 0;
+        __syncthreads();
+    }
+    const int q0 = blockIdx.x * kBoxBlock, q1 = min(n, q0 + kBoxBlock);
+    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+        const int key = box_key(pts + (int64_t)q * 3, gout[q], g, L);
+        if (key >= 0) atomicAdd(sh ? &hist[key] : &counts[key], 1u);
+    }
+    if (sh) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < g.nbins; i += blockDim.x)
+            if (hist[i]) atomicAdd(&counts[i], hist[i]);
+    }
+}
+
+// one CTA: bin_start = exclusive prefix of the counts (nbins + 1 entries), item_start = exclusive
+// prefix of the work items ceil(count / chunk), cursor = bin_start; counts reset to zero
+__global__ void __launch_bounds__(1024) k_box_scan(unsigned *__restrict__ counts, int nbins, int chunk,
+                                                   int *__restrict__ bin_start, int *__restrict__ item_start,
+                                                   unsigned *__restrict__ cursor)
+{
+    __shared__ unsigned sq[1024], si[1024];
+    const int t = threadIdx.x;
+    const int per = (nbins + 1023) / 1024, b0 = min(nbins, t * per), b1 = min(nbins, b0 + per);
+    unsigned cq = 0, ci = 0;
+    for (int b = b0; b < b1; ++b) {
+        cq += counts[b];
+        ci += (counts[b] + chunk - 1) / chunk;
+    }
+    sq[t] = cq;
+    si[t] = ci;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const unsigned aq = t >= off ? sq[t - off] : 0u, ai = t >= off ? si[t - off] : 0u;
+        __syncthreads();
+        sq[t] += aq;
+        si[t] += ai;
+        __syncthreads();
+    }
+    unsigned pq = sq[t] - cq, pi = si[t] - ci;
+    for (int b = b0; b < b1; ++b) {
+        const unsigned c = counts[b];
+        bin_start[b] = (int)pq;
+        item_start[b] = (int)pi;
+        cursor[b] = pq;
+        pq += c;
+        pi += (c + chunk - 1) / chunk;
+        counts[b] = 0;
+    }
+    if (t == 1023) {
+        bin_start[nbins] = (int)sq[1023];
+        item_start[nbins] = (int)si[1023];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_box_scatter(const float *__restrict__ pts, const float *__restrict__ gout, int n,
+                                                     BoxGeom g, ibl::Layout L, unsigned *__restrict__ cursor,
+                                                     float4 *__restrict__ q4)
+{
+    __shared__ unsigned cnt[kBoxSharedBins], base[kBoxSharedBins];
+    const bool sh = g.nbins <= kBoxSharedBins;
+    const int q0 = blockIdx.x * kBoxBlock, q1 = min(n, q0 + kBoxBlock);
+    if (sh) {
+        for (int i = threadIdx.x; i < g.nbins; i += blockDim.x) cnt[i] = 0;
+        __syncthreads();
+        for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+            const int key = box_key(pts + (int64_t)q * 3, gout[q], g, L);
+            if (key >= 0) atomicAdd(&cnt[key], 1u);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < g.nbins; i += blockDim.x) {
+            const unsigned c = cnt[i];
+            base[i] = c ? atomicAdd(&cursor[i], c) : 0u;
+            cnt[i] = 0;
+        }
+        __syncthreads();
+    }
+    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+        const float *p = pts + (int64_t)q * 3;
+        const float w = gout[q];
+        const int key = box_key(p, w, g, L);
+        if (key < 0) continue;
+        const unsigned pos = sh ? base[key] + atomicAdd(&cnt[key], 1u) : atomicAdd(&cursor[key], 1u);
+        q4[pos] = make_float4(p[0], p[1], p[2], w);
+    }
+}
+
+// the geometry of the bins for handle h, and whether a call of npts queries takes the binned adjoint
+bool box_plan(const interp *h, int64_t npts, BoxGeom &g)
+{
+    const SplineOps *o = h->ops;
+    if (!o->adjoint_box || h->opt_adjoint_bins == 0 || npts > INT32_MAX) return false;
+    g.D = o->D;
+    g.H2 = 2 * o->halo;
+    g.lb = o->box_lb;
+    int64_t nb = 1;
+    for (int a = 0; a < 3; ++a) {
+        g.nb[a] = (h->lay32.pdims[a] + (1 << g.lb) - 1) >> g.lb;
+        nb *= g.nb[a];
+    }
+    if (nb > (1 << 24)) return false;
+    g.nbins = (int)nb;
+    if (h->opt_adjoint_bins == 1) return true;
+    // worth it when the contributions far outnumber the boxes' global atomics: every bin's box
+    // (of M (2^lb + 2 halo + 2)^3 sites) is added once
+    const int W = (1 << g.lb) + g.H2 + 2;
+    const double box_sites = (double)o->M * W * W * W;
+    return (double)npts * o->lookups >= 2.0 * (double)g.nbins * box_sites;
+}
+
+}  // namespace
+
+// dL/dc into h->dpad on spatially binned queries; false (nothing enqueued, error cleared) when the
+// scratch cannot be had or the stream is capturing
+static bool adjoint_box_launch(const interp *h, const BoxGeom &g, const float *pts, int64_t npts, const float *gout,
+                               cudaStream_t st, cudaError_t &err)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return false;
+    }
+    const int n = (int)npts;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t nb = (size_t)g.nbins;
+    const size_t sz[] = {up((size_t)n * 16), up(nb * 4), up((nb + 1) * 4), up((nb + 1) * 4), up(nb * 4)};
+    size_t bytes = 0;
+    for (size_t b : sz) bytes += b;
+    cudaMemPool_t pool = nullptr;
+    void *block = nullptr;
+    if (ps_pool(h->device, &pool) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    g_dev_allocs.fetch_add(1, std::memory_order_relaxed);
+    if (cudaMallocFromPoolAsync(&block, bytes, pool, st) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    unsigned char *p = static_cast<unsigned char *>(block);
+    float4 *q4 = reinterpret_cast<float4 *>(p);
+    unsigned *counts = reinterpret_cast<unsigned *>(p + sz[0]);
+    int *bin_start = reinterpret_cast<int *>(p + sz[0] + sz[1]);
+    int *item_start = reinterpret_cast<int *>(p + sz[0] + sz[1] + sz[2]);
+    unsigned *cursor = reinterpret_cast<unsigned *>(p + sz[0] + sz[1] + sz[2] + sz[3]);
+    cudaError_t e = cudaMemsetAsync(counts, 0, nb * 4, st);
+    const unsigned grid = (unsigned)((n + kBoxBlock - 1) / kBoxBlock);
+    if (e == cudaSuccess) {
+        k_box_count<<<grid, 256, 0, st>>>(pts, gout, n, g, h->lay32, counts);
+        k_box_scan<<<1, 1024, 0, st>>>(counts, g.nbins, kBoxChunk, bin_start, item_start, cursor);
+        k_box_scatter<<<grid, 256, 0, st>>>(pts, gout, n, g, h->lay32, cursor, q4);
+        e = cudaPeekAtLastError();
+    }
+    if (e == cudaSuccess) {
+        ibr::BoxArgs a;
+        a.q4 = q4;
+        a.bin_start = bin_start;
+        a.item_start = item_start;
+        a.nbins = g.nbins;
+        for (int i = 0; i < 3; ++i) a.nb[i] = g.nb[i];
+        a.chunk = kBoxChunk;
+        a.max_items = g.nbins + (n + kBoxChunk - 1) / kBoxChunk;
+        e = h->ops->adjoint_box(a, h->lay32, h->dpad, st);
+    }
+    cudaFreeAsync(block, st);
+    err = e;
+    return true;
+}
+
+// dL/dc into h->dpad: the binned adjoint where it applies (3-D splines with few pieces, many
+// queries); multi-piece splines with large pieces take the pre-sort like eval_launch (the
+// adjoint's atomic scatter has no fixed summation order either way)
 static cudaError_t adjoint_launch(const interp *h, const float *pts, int64_t npts, const float *gout, cudaStream_t st)
 {
+    BoxGeom g;
+    cudaError_t eb = cudaSuccess;
+    if (box_plan(h, npts, g) && adjoint_box_launch(h, g, pts, npts, gout, st, eb)) return eb;
     PresortWs w;
-    if (h->ops->K < 4 || !presort_wanted(h->ops, npts) || !ps_acquire(h, npts, st, w))
+    if (h->ops->K < 4 || !presort_wanted(h, npts) || !ps_acquire(h, npts, st, w))
         return h->ops->adjoint(pts, npts, gout, h->lay32, h->dpad, st);
     const int s = h->s;
     cudaError_t e = cudaSuccess;
@@ -626,7 +870,12 @@ bool ps_acquire(const interp *h, int64_t npts, cudaStream_t st, PresortWs &w)
     size_t bytes = 0;
     for (size_t b : sz) bytes += b;
     cudaMemPool_t pool = nullptr;
-    if (ps_pool(h->device, &pool) != cudaSuccess || cudaMallocFromPoolAsync(&w.block, bytes, pool, st) != cudaSuccess) {
+    if (ps_pool(h->device, &pool) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    g_dev_allocs.fetch_add(1, std::memory_order_relaxed);
+    if (cudaMallocFromPoolAsync(&w.block, bytes, pool, st) != cudaSuccess) {
         cudaGetLastError();
         w.block = nullptr;
         return false;
@@ -651,7 +900,7 @@ cudaError_t ps_sort_chunk(const interp *h, PresortWs &w, const float *pts, const
     const SplineOps *ops = h->ops;
     cudaError_t e = ops->debug(pts, m, h->lay32, nullptr, w.piece, st);
     if (e != cudaSuccess) return e;
-    const unsigned gc = (unsigned)std::min<int64_t>((m + 255) / 256, 148 * 8);
+    const unsigned gc = (unsigned)std::min<int64_t>((m + 255) / 256, (int64_t)h->sms * 8);
     k_ps_count<<<gc, 256, 0, st>>>(w.piece, m, ops->M, w.c, ops->K, w.nkeys, w.key, w.total);
     k_ps_scan<<<1, kPsMaxKeys, 0, st>>>(w.total, w.cursor, w.nkeys);
     const unsigned gs = (unsigned)((m + kPsBlock - 1) / kPsBlock);
@@ -685,19 +934,32 @@ static interp_status create_handle(const SplineOps *ops, const int32_t *dims, in
         cc *= dims[a];
     }
     const int esz = storage == INTERP_F32 ? 4 : 2;
-    // cosets side by side in the bricks or in separate arrays: separate by default (measured
-    // faster on the BCC quintic workload); INTERP_B300_INTERLEAVE=1 selects the other layout
-    const char *il = std::getenv("INTERP_B300_INTERLEAVE");
-    const bool inter = il && il[0] == '1';
-    if (!ibl::make_layout(h->lay, s, h->dims, pad, esz, ops->M, inter) ||
-        !ibl::make_layout(h->lay32, s, h->dims, pad, 4, ops->M, inter)) {
+    // cosets in separate bricked arrays (the kernels' brick widths are compile-time constants of
+    // this layout; cosets side by side inside the bricks measured slower on the BCC quintic
+    // workload: 15.1 against 13.4 L1 misses per query)
+    if (!ibl::make_layout(h->lay, s, h->dims, pad, esz, ops->M, false) ||
+        !ibl::make_layout(h->lay32, s, h->dims, pad, 4, ops->M, false)) {
         delete h;
         return INTERP_ESIZE;
     }
     h->coeff_count = cc * ops->M;
     cudaGetDevice(&h->device);
+    if (cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || h->sms < 1) {
+        cudaGetLastError();
+        h->sms = 148;
+    }
+    // initial launch options from the environment (read once, here)
+    auto env01 = [](const char *name) {
+        const char *e = std::getenv(name);
+        return e ? (e[0] == '1' ? 1 : 0) : -1;
+    };
+    h->opt_binned = env01("INTERP_B300_BINNED");
+    h->opt_presort = env01("INTERP_B300_PRESORT");
+    h->opt_dense = env01("INTERP_B300_DENSE");
+    h->opt_adjoint_bins = env01("INTERP_B300_ADJOINT_BINS");
+    if (const char *e = std::getenv("INTERP_B300_BINCFG")) h->opt_bin_small = e[0] == 's' ? 1 : 0;
     const size_t bytes = (size_t)h->lay.total * esz;
-    cudaError_t e = cudaMalloc(&h->coeffs, bytes);
+    cudaError_t e = lib_malloc(&h->coeffs, bytes);
     if (e == cudaSuccess) e = cudaMemset(h->coeffs, 0, bytes);
     if (e != cudaSuccess) {
         cudaFree(h->coeffs);
@@ -725,6 +987,8 @@ const char *interp_strerror(interp_status st)
 }
 
 int interp_num_splines(void) { return (int)registry().size(); }
+
+long long interp_debug_device_allocations(void) { return g_dev_allocs.load(std::memory_order_relaxed); }
 
 const char *interp_spline_name(int i)
 {
@@ -815,6 +1079,36 @@ interp_status interp_info(const interp_t *h, interp_info_t *info)
     return INTERP_OK;
 }
 
+interp_status interp_set_option(interp_t *h, const char *name, int value)
+{
+    if (!h || !name) return INTERP_EINVAL;
+    int *slot = nullptr;
+    int lo = -1;
+    if (std::strcmp(name, "binned") == 0) slot = &h->opt_binned;
+    else if (std::strcmp(name, "presort") == 0) slot = &h->opt_presort;
+    else if (std::strcmp(name, "dense") == 0) slot = &h->opt_dense;
+    else if (std::strcmp(name, "adjoint_bins") == 0) slot = &h->opt_adjoint_bins;
+    else if (std::strcmp(name, "bin_small_tiles") == 0) {
+        slot = &h->opt_bin_small;
+        lo = 0;
+    }
+    if (!slot || value < lo || value > 1) return INTERP_EINVAL;
+    *slot = value;
+    return INTERP_OK;
+}
+
+interp_status interp_get_option(const interp_t *h, const char *name, int *value)
+{
+    if (!h || !name || !value) return INTERP_EINVAL;
+    if (std::strcmp(name, "binned") == 0) *value = h->opt_binned;
+    else if (std::strcmp(name, "presort") == 0) *value = h->opt_presort;
+    else if (std::strcmp(name, "dense") == 0) *value = h->opt_dense;
+    else if (std::strcmp(name, "adjoint_bins") == 0) *value = h->opt_adjoint_bins;
+    else if (std::strcmp(name, "bin_small_tiles") == 0) *value = h->opt_bin_small;
+    else return INTERP_EINVAL;
+    return INTERP_OK;
+}
+
 interp_status interp_prefilter(interp_t *h, const float *samples, int ntaps, const int32_t *taps, const float *weights,
                                void *stream)
 {
@@ -901,7 +1195,7 @@ interp_status interp_set_coeffs(interp_t *h, const void *src, interp_dtype src_d
     void *tmp = nullptr;
     cudaError_t e = cudaSuccess;
     if (!src_on_device) {
-        e = cudaMallocAsync(&tmp, bytes, st);
+        e = lib_malloc_async(&tmp, bytes, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) {
             if (tmp) cudaFreeAsync(tmp, st);
@@ -910,7 +1204,7 @@ interp_status interp_set_coeffs(interp_t *h, const void *src, interp_dtype src_d
         }
         dsrc = tmp;
     }
-    const unsigned grid = (unsigned)std::min<int64_t>((h->coeff_count + 255) / 256, 148 * 32);
+    const unsigned grid = (unsigned)std::min<int64_t>((h->coeff_count + 255) / 256, (int64_t)h->sms * 32);
 #define PADCOPY(ST, CT) \
     k_pad_copy<ST, CT><<<grid, 256, 0, st>>>(static_cast<const ST *>(dsrc), static_cast<CT *>(h->coeffs), h->coeff_count, h->lay)
 #define PADCOPY_SRC(CT)                                              \
@@ -978,7 +1272,7 @@ interp_status interp_eval_host(interp_t *h, const float *pts, int64_t npts, floa
     const int64_t slot_floats = kChunk * (s + 1 + s);     // points, values, gradients
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < NS && e == cudaSuccess; ++i) {
-        if (!h->stage[i]) e = cudaMalloc(&h->stage[i], (size_t)slot_floats * sizeof(float));
+        if (!h->stage[i]) e = lib_malloc(&h->stage[i], (size_t)slot_floats * sizeof(float));
         if (e == cudaSuccess && !h->hs[i]) e = cudaStreamCreateWithFlags(&h->hs[i], cudaStreamNonBlocking);
     }
     for (int i = 0; i < NS + 1 && e == cudaSuccess; ++i)
@@ -1029,7 +1323,7 @@ interp_status interp_backward(interp_t *h, const float *pts, int64_t npts, const
     cudaError_t e = cudaSuccess;
     const size_t dbytes = (size_t)h->lay32.total * sizeof(float);
     if (!h->dpad) {
-        e = cudaMalloc(&h->dpad, dbytes);
+        e = lib_malloc(&h->dpad, dbytes);
         if (e != cudaSuccess) {
             h->dpad = nullptr;
             cudaGetLastError();
@@ -1039,7 +1333,7 @@ interp_status interp_backward(interp_t *h, const float *pts, int64_t npts, const
     e = cudaMemsetAsync(h->dpad, 0, dbytes, st);
     if (e == cudaSuccess) e = adjoint_launch(h, pts, npts, gout, st);
     if (e == cudaSuccess) {
-        const unsigned grid = (unsigned)std::min<int64_t>((h->coeff_count + 255) / 256, 148 * 32);
+        const unsigned grid = (unsigned)std::min<int64_t>((h->coeff_count + 255) / 256, (int64_t)h->sms * 32);
         k_unpad_add<<<grid, 256, 0, st>>>(h->dpad, dcoeffs, h->coeff_count, h->lay32);
         e = cudaPeekAtLastError();
     }
@@ -1065,7 +1359,7 @@ interp_status interp_eval_rays(const interp_t *h, const interp_rays_t *rays, int
     rg.width = rays->width;
     rg.height = rays->height;
     rg.steps = rays->steps;
-    cudaError_t e = h->ops->rays[with_grad ? 1 : 0](rg, h->coeffs, h->lay, out, pts_out,
+    cudaError_t e = h->ops->rays[with_grad ? 1 : 0](rg, h->coeffs, h->lay, out, pts_out, launch_flags(h),
                                                       static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) cudaGetLastError();
     return cuda_status(e);
@@ -1075,8 +1369,9 @@ interp_status interp_backward_noalloc(interp_t *h, const float *pts, int64_t npt
                                       float *dpts, void *stream)
 {
     if (!h || npts < 0) return INTERP_EINVAL;
+    // the static array's limit concerns dL/dc only: a dpts-only call never touches it
     const int64_t need = (int64_t)h->lay32.total;
-    if (need > INTERP_NOALLOC_MAX_GRAD_ELEMS) return INTERP_ESIZE;
+    if (dcoeffs && need > INTERP_NOALLOC_MAX_GRAD_ELEMS) return INTERP_ESIZE;
     if (npts == 0) return INTERP_OK;
     if (!pts || !gout) return INTERP_EINVAL;
     if (npts > (int64_t)INT32_MAX * kTPB) return INTERP_ESIZE;
@@ -1086,19 +1381,23 @@ interp_status interp_backward_noalloc(interp_t *h, const float *pts, int64_t npt
         return INTERP_ECUDA;
     }
     if (dev != h->device) return INTERP_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (dpts) {
-        interp_status s2 = eval_common(h, pts, npts, nullptr, dpts, gout, 2, stream);
-        if (s2 != INTERP_OK) return s2;
+        // the pullback without the piece pre-sort, whose scratch comes from the library's pool
+        const cudaError_t e2 = eval_launch(h, pts, npts, nullptr, dpts, gout, 2, st, false);
+        if (e2 != cudaSuccess) {
+            cudaGetLastError();
+            return cuda_status(e2);
+        }
     }
     if (!dcoeffs) return INTERP_OK;
     float *scratch = nullptr;
     interp_status st0 = noalloc_scratch(dev, &scratch);
     if (st0 != INTERP_OK) return st0;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(scratch, 0, (size_t)need * sizeof(float), st);
     if (e == cudaSuccess) e = h->ops->adjoint(pts, npts, gout, h->lay32, scratch, st);
     if (e == cudaSuccess) {
-        const unsigned grid = (unsigned)std::min<int64_t>((h->coeff_count + 255) / 256, 148 * 32);
+        const unsigned grid = (unsigned)std::min<int64_t>((h->coeff_count + 255) / 256, (int64_t)h->sms * 32);
         k_unpad_add<<<grid, 256, 0, st>>>(scratch, dcoeffs, h->coeff_count, h->lay32);
         e = cudaPeekAtLastError();
     }
@@ -1131,7 +1430,7 @@ interp_status interp_sort_points(interp_t *h, const float *pts, int64_t npts, in
         h->sort_keys = nullptr;
         h->sort_nkeys = 0;
         // the counters, then one partial sum per 4096 counters for the scan
-        e = cudaMalloc(&h->sort_keys, ((size_t)nkeys + nkeys / 4096 + 1) * sizeof(unsigned));
+        e = lib_malloc(&h->sort_keys, ((size_t)nkeys + nkeys / 4096 + 1) * sizeof(unsigned));
         if (e != cudaSuccess) {
             h->sort_keys = nullptr;
             cudaGetLastError();
@@ -1283,11 +1582,11 @@ interp_status interp_batch_create(const interp_batch_item *items, int n, interp_
         if (gi == 0) b->tiles.emplace(it.vol->ops->name, kDefaultTile);
         else b->own.push_back(it.vol);
     }
-    cudaError_t e = cudaMalloc(&b->d_counters, 2 * sizeof(unsigned long long));
+    cudaError_t e = lib_malloc(&b->d_counters, 2 * sizeof(unsigned long long));
     for (int gi = 0; gi < 2 && e == cudaSuccess; ++gi) {
         auto &G = b->g[gi];
         if (G.vols.empty()) continue;
-        e = cudaMalloc(&G.d_vols, G.vols.size() * sizeof(ibl::BatchVol));
+        e = lib_malloc(&G.d_vols, G.vols.size() * sizeof(ibl::BatchVol));
         if (e == cudaSuccess && gi == 0) e = ibr::batch_grid_3d(&G.grid);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking);

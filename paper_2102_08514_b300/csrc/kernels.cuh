@@ -199,16 +199,83 @@ constexpr uint64_t cosets_packed()
 }
 
 // one slot of the folded offset: |y| and what the gather needs about the original axis it came
-// from (sign, within-brick coordinate of the cell, brick geometry of that axis)
+// from.  d[] holds, for the folded offsets o = -2, -1, +1, +2 along the slot, the element-offset
+// change from the cell's own site to the site o steps away (o steps along the slot are sg * o
+// steps along the original axis; in the bricked layout the change depends on the cell's
+// within-brick coordinate p).  The deltas are formed once per axis before the sort and travel
+// with the slot, so each stencil site's address is the fold's base plus one delta per nonzero
+// offset; entries a spline never uses are dead code.
 struct Slot {
     float y;
-    int sg;   // +1 / -1: sign of y along the original axis
-    int ax;   // original axis
-    int p;    // within-brick coordinate of the cell's padded index along that axis
-    int lb;   // log2 brick width of that axis
-    int bs;   // brick stride of that axis
-    int wt;   // within-brick weight of that axis
+    int sg;     // +1 / -1: sign of y along the original axis
+    int ax;     // original axis
+    int p;      // within-brick coordinate of the cell's padded index along that axis
+    int d[4];   // offset deltas of o = -2, -1, +1, +2 (index o + 2, or o + 1 for o > 0)
 };
+
+constexpr int delta_index(int o) { return o < 0 ? o + 2 : o + 1; }
+
+// element-offset change of a step of D sites along an axis of brick width 2^LB, brick stride bs
+// and within-brick weight wt, from a site whose within-brick coordinate is e (0 <= e < 2^LB)
+template <int LB, int D>
+__device__ __forceinline__ int brick_delta(int e, int bs, int wt)
+{
+    if constexpr (LB == 0) {
+        return D * bs;
+    } else if constexpr (LB == 1 && (D == 2 || D == -2)) {
+        return D / 2 * bs;
+    } else if constexpr (LB == 1 && D == 1) {
+        return wt + e * (bs - 2 * wt);              // e = 0: next site in the brick; e = 1: next brick
+    } else if constexpr (LB == 1 && D == -1) {
+        return wt - bs + e * (bs - 2 * wt);         // e = 0: previous brick; e = 1: previous site
+    } else {
+        constexpr int W = 1 << LB;
+        const int v = e + D;
+        return (v >> LB) * bs + ((v & (W - 1)) - e) * wt;
+    }
+}
+
+// the same with a run-time brick width (the binned kernels rebuild slots from packed records)
+__device__ __forceinline__ int brick_delta_rt(int e, int D, int lb, int bs, int wt)
+{
+    const int v = e + D;
+    return (v >> lb) * bs + ((v & ((1 << lb) - 1)) - e) * wt;
+}
+
+// whether any stencil site of any piece of SP lies o steps from the cell along some folded slot
+template <class SP>
+constexpr bool uses_offset(int o)
+{
+    for (int j = 0; j < SP::K; ++j)
+        for (int m = 0; m < SP::NS[j]; ++m)
+            for (int a = 0; a < SP::S; ++a)
+                if (SP::SITE[j][m][a] == o) return true;
+    return false;
+}
+
+// the deltas of slot sl for the offsets SP uses, given its sign and within-brick coordinate e
+template <class SP, int LB>
+__device__ __forceinline__ void slot_deltas(Slot &sl, int e, int bs, int wt)
+{
+    sfor<2>([&](auto I) {
+        constexpr int o = decltype(I)::value + 1;   // |o| = 1, 2
+        if constexpr (uses_offset<SP>(o) || uses_offset<SP>(-o)) {
+            const int fwd = brick_delta<LB, o>(e, bs, wt), bwd = brick_delta<LB, -o>(e, bs, wt);
+            if constexpr (uses_offset<SP>(o)) sl.d[delta_index(o)] = sl.sg > 0 ? fwd : bwd;
+            if constexpr (uses_offset<SP>(-o)) sl.d[delta_index(-o)] = sl.sg > 0 ? bwd : fwd;
+        }
+    });
+}
+
+template <class SP>
+__device__ __forceinline__ void slot_deltas_rt(Slot &sl, int lb, int bs, int wt)
+{
+    sfor<2>([&](auto I) {
+        constexpr int o = decltype(I)::value + 1;
+        if constexpr (uses_offset<SP>(o)) sl.d[delta_index(o)] = brick_delta_rt(sl.p, sl.sg * o, lb, bs, wt);
+        if constexpr (uses_offset<SP>(-o)) sl.d[delta_index(-o)] = brick_delta_rt(sl.p, -sl.sg * o, lb, bs, wt);
+    });
+}
 
 // Ties are decided as for the point x + eps v, eps -> 0+, with the fixed world direction
 // v = (1, 2^-12, 2^-24, 2^-36) (the direction the oracle uses), so that every coset takes the same
@@ -261,40 +328,86 @@ template <class CT> struct DevVol {
 };
 
 template <int S> struct Fold {
-    int base;           // element offset of the brick holding the cell's site (coset included)
+    int base;           // element offset of the cell's own site (coset included)
     float t[S];         // folded offset y' (before the anchor shift)
-    Slot sl[S];         // per folded slot: sign, original axis and brick geometry
+    Slot sl[S];         // per folded slot: sign, original axis, offset deltas
     int piece;
     bool in_range;
 };
 
-// element offset, relative to Fold::base, of the site displaced by o along folded slot A
-__device__ __forceinline__ int slot_term(const Slot &sl, int o)
+// element offset, relative to Fold::base, of the site displaced by a run-time o along folded
+// slot sl, whose axis has brick width 2^lb, brick stride bs and within-brick weight wt
+__device__ __forceinline__ int slot_term_rt(const Slot &sl, int o, int lb, int bs, int wt)
 {
-    const int v = sl.p + sl.sg * o;
-    return (v >> sl.lb) * sl.bs + (v & ((1 << sl.lb) - 1)) * sl.wt;
+    return brick_delta_rt(sl.p, sl.sg * o, lb, bs, wt);
 }
 
-// side of plane I for the folded offset in the slots, exactly: the sum in FP64 with the terms in
-// descending order (y' sorted) is exact or keeps its sign; exactly on the plane, the side of
-// y' + eps v' with v' the folded image of the world direction v (the term of the smallest
-// original axis decides, v being lexicographic)
+// log2 brick width of axis a of the S-axis layout of SP's cosets with element type CT
+template <class SP, class CT>
+constexpr int axis_lb(int a)
+{
+    return ibl::brick_lb(SP::S, (int)sizeof(CT), SP::M, false, a);
+}
+
+// Knuth's TwoSum: s + e == a + b exactly, s = fl(a + b) (round to nearest; the _rn intrinsics
+// keep the compiler from contracting or reassociating the steps)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// sign (-1, 0, +1) of the exact sum of N FP32 terms, in FP32 only: Shewchuk's grow-expansion
+// keeps the running sum as an expansion of N nonoverlapping components (increasing magnitude,
+// zeros allowed) whose exact sum is the exact sum of the terms; the sign of a nonoverlapping
+// expansion is the sign of its largest nonzero component.  No overflow for the plane tests
+// (terms of magnitude <= 5/2).
+template <int N>
+__device__ __forceinline__ int exact_sum_sign(const float (&t)[N])
+{
+    float e[N];
+    e[0] = t[0];
+    sfor<N - 1>([&](auto I) {
+        constexpr int m = decltype(I)::value + 1;          // components so far
+        float q = t[m];
+        sfor<m>([&](auto J) {
+            float s, h;
+            two_sum(q, e[J], s, h);
+            e[J] = h;
+            q = s;
+        });
+        e[m] = q;
+    });
+    int sg = 0;
+    sfor<N>([&](auto J) {
+        if (e[J] != 0.0f) sg = e[J] > 0.0f ? 1 : -1;       // the last nonzero is the largest
+    });
+    return sg;
+}
+
+// side of plane I for the folded offset in the slots, exactly (FP32 error-free sums: the terms
+// are +-y'_a and -e); exactly on the plane, the side of y' + eps v' with v' the folded image of
+// the world direction v (the term of the smallest original axis decides, v being lexicographic)
 template <class SP, int I, int S>
 __device__ __forceinline__ bool plane_side_exact(const Slot (&sl)[S])
 {
-    double d = -(double)SP::PLANE_E[I];
+    float terms[S + 1];
+    terms[0] = -SP::PLANE_E[I];
     int best_ax = 99, sgn = 1;
     sfor<S>([&](auto A) {
         constexpr int p = SP::PLANE_P[I][decltype(A)::value];
+        static_assert(p >= -1 && p <= 1, "plane normals have entries in {-1, 0, 1}");
+        terms[1 + A] = p > 0 ? sl[A].y : (p < 0 ? -sl[A].y : 0.0f);
         if constexpr (p != 0) {
-            d = fma((double)p, (double)sl[A].y, d);
             if (sl[A].ax < best_ax) {
                 best_ax = sl[A].ax;
                 sgn = p * sl[A].sg;
             }
         }
     });
-    return d != 0.0 ? d > 0.0 : sgn > 0;
+    const int d = exact_sum_sign<S + 1>(terms);
+    return d != 0 ? d > 0 : sgn > 0;
 }
 
 // steps 1-3 for coset K of spline SP (K < 0: the run-time coset index kr)
@@ -308,7 +421,7 @@ __device__ __forceinline__ Fold<SP::S> fold_coset(const float (&x)[SP::S], const
     int base = (K >= 0 ? K : kr) * v.L.kw;
     sfor<S>([&](auto A) {
         constexpr int a = decltype(A)::value;
-        const int lb = v.L.lb[a];
+        constexpr int LB = axis_lb<SP, CT>(a);      // the layout's brick width (make_layout)
         int idx;
         float y;
         if constexpr (K >= 0) {
@@ -322,15 +435,15 @@ __device__ __forceinline__ Fold<SP::S> fold_coset(const float (&x)[SP::S], const
         }
         ok &= (unsigned)(idx + H) < (unsigned)(v.L.n[a] + 2 * H);
         const int P = idx + 2 * H;                       // padded index of the cell's site
-        base += (P >> lb) * v.L.bstride[a];
+        const int e = P & ((1 << LB) - 1);
+        const int bs = v.L.bstride[a], wt = v.L.wt[a];
+        base += (P >> LB) * bs + e * wt;
         Slot &sl = f.sl[a];
         sl.y = fabsf(y);
         sl.sg = (y < 0.0f) ? -1 : 1;
         sl.ax = a;
-        sl.p = P & ((1 << lb) - 1);
-        sl.lb = lb;
-        sl.bs = v.L.bstride[a];
-        sl.wt = v.L.wt[a];
+        sl.p = e;
+        slot_deltas<SP, LB>(sl, e, bs, wt);
     });
     sort_desc<S, (SP::SMOOTH < 1)>(f.sl);
     sfor<S>([&](auto A) { f.t[A] = f.sl[A].y; });
@@ -371,16 +484,36 @@ __device__ __forceinline__ Fold<SP::S> fold_coset(const float (&x)[SP::S], const
     return f;
 }
 
-// element offset (relative to Fold::base) of stencil site M of piece J
+// element offset (relative to Fold::base) of stencil site M of piece J: one delta per slot with
+// a nonzero offset
 template <class SP, int J, int M>
 __device__ __forceinline__ int site_offset(const Fold<SP::S> &f)
 {
     int off = 0;
     sfor<SP::S>([&](auto A) {
         constexpr int g = SP::SITE[J][M][decltype(A)::value];
-        off += slot_term(f.sl[A], g);
+        static_assert(g >= -2 && g <= 2, "stencil offsets lie within two sites of the cell");
+        if constexpr (g != 0) off += f.sl[A].d[delta_index(g)];
     });
     return off;
+}
+
+// gradient back through the fold: d/dx_ax += sign * d/dy'_slot, for each original axis the one
+// slot that came from it
+template <int S>
+__device__ __forceinline__ void unfold_grad(const Fold<S> &f, const float (&gy)[S], float (&grad)[S])
+{
+    float gs[S];
+    sfor<S>([&](auto A) { gs[A] = (f.sl[A].sg < 0) ? -gy[A] : gy[A]; });
+    sfor<S>([&](auto B) {
+        constexpr int b = decltype(B)::value;
+        float g = gs[S - 1];
+        sfor<S - 1>([&](auto A) {
+            constexpr int a = S - 2 - decltype(A)::value;
+            if (f.sl[a].ax == b) g = gs[a];
+        });
+        grad[b] += g;
+    });
 }
 
 // steps 4-5 for piece J: accumulate f (and grad f if GRAD) into the query's sums
@@ -451,11 +584,7 @@ __device__ __forceinline__ void eval_piece(const Fold<SP::S> &f, const DevVol<CT
     }
     if constexpr (GRAD) {
         val += r.v;
-        // back through the fold: d/dx_ax = sign * d/dy'_slot
-        sfor<S>([&](auto A) {
-            const float gs = (f.sl[A].sg < 0) ? -r.g[A] : r.g[A];
-            sfor<S>([&](auto B) { grad[B] += (f.sl[A].ax == B) ? gs : 0.0f; });
-        });
+        unfold_grad<S>(f, r.g, grad);
     }
 }
 
@@ -480,7 +609,20 @@ __device__ __forceinline__ void eval_piece_dense(const Fold<SP::S> &f, const Dev
 #pragma unroll 1
     for (int m = 0; m < ns; ++m) {
         int off = 0;
-        sfor<S>([&](auto Ax) { off += slot_term(f.sl[Ax], (int)__ldg(g + m * S + Ax)); });
+        sfor<S>([&](auto Ax) {
+            // the brick geometry of the slot's axis, selected without dynamic indexing
+            const int ax = f.sl[Ax].ax;
+            int lb = v.L.lb[0], bs = v.L.bstride[0], wt = v.L.wt[0];
+            sfor<S - 1>([&](auto B) {
+                constexpr int b = 1 + decltype(B)::value;
+                if (ax == b) {
+                    lb = v.L.lb[b];
+                    bs = v.L.bstride[b];
+                    wt = v.L.wt[b];
+                }
+            });
+            off += slot_term_rt(f.sl[Ax], (int)__ldg(g + m * S + Ax), lb, bs, wt);
+        });
         const float cm = load_coef<CT>(cb + off);
         sfor<NM4>([&](auto Q) {
             constexpr int q = decltype(Q)::value;
@@ -500,10 +642,7 @@ __device__ __forceinline__ void eval_piece_dense(const Fold<SP::S> &f, const Dev
     } else {
         const VG<S> r = horner_grad<S, S, DEG, 0, NM>(b, t);
         val += r.v;
-        sfor<S>([&](auto Ax) {
-            const float gs = (f.sl[Ax].sg < 0) ? -r.g[Ax] : r.g[Ax];
-            sfor<S>([&](auto B) { grad[B] += (f.sl[Ax].ax == B) ? gs : 0.0f; });
-        });
+        unfold_grad<S>(f, r.g, grad);
     }
 }
 
@@ -844,17 +983,16 @@ __device__ __forceinline__ Fold<SP::S> unpack_rec(const BinRec<SP::S> &r, const 
         sl.ax = (int)((b >> 1) & 3u);
         sl.p = (int)(b >> 3);
         // the brick geometry of the slot's axis, selected without dynamic indexing
-        sl.lb = v.L.lb[0];
-        sl.bs = v.L.bstride[0];
-        sl.wt = v.L.wt[0];
+        int lb = v.L.lb[0], bs = v.L.bstride[0], wt = v.L.wt[0];
         sfor<S - 1>([&](auto B) {
             constexpr int ax = 1 + decltype(B)::value;
             if (sl.ax == ax) {
-                sl.lb = v.L.lb[ax];
-                sl.bs = v.L.bstride[ax];
-                sl.wt = v.L.wt[ax];
+                lb = v.L.lb[ax];
+                bs = v.L.bstride[ax];
+                wt = v.L.wt[ax];
             }
         });
+        slot_deltas_rt<SP>(sl, lb, bs, wt);
     });
     return f;
 }
@@ -1428,6 +1566,138 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_priv(const float *__restrict
             r /= ld[ax];
         }
         atomicAdd(dpad + ibl::elem_offset(v.L, k, p), a);
+    }
+}
+
+// ------------------------------------------------------------------------------------ adjoint on spatial bins
+//
+// The adjoint of random queries sorted by cell (the caller's call runs a counting sort of the
+// queries into spatial bins first, see interp_backward): a bin holds the queries whose coset-0
+// cell has padded index P in [b B, (b + 1) B) along every axis (B = 2^LB cells).  Every site such
+// a query touches, on any coset, lies in the box [b B - 1 - HALO, (b + 1) B + HALO] per axis (the
+// other cosets' cells are the coset-0 cell or the one below it, D <= 2), so a CTA sums a bin's
+// contributions in a shared-memory copy of that box and adds the box to the padded gradient
+// buffer once, one global atomic per touched site instead of one per (query, site).
+// Work items are chunks of at most `chunk` queries of one bin (a bin with many queries is split
+// so that clustered queries still spread over the GPU).
+// bin of a query for the spatially binned adjoint: the coset-0 cell's padded index per axis
+// (the same exact reduction as the kernels), 2^lb cells per bin; -1 for a query that adds
+// nothing (non-finite, gout = 0, or its cell outside the padded arrays, so every coset out of
+// range)
+template <int D>
+__device__ __forceinline__ int box_key3(const float (&x)[3], float w, int H2, const ibl::Layout &L, int lb, const int (&nb)[3])
+{
+    if (!(isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2])) || w == 0.0f) return -1;
+    int key = 0;
+    bool in = true;
+    sfor<3>([&](auto A) {
+        constexpr int a = decltype(A)::value;
+        int i;
+        float y;
+        reduce_axis<D, 0>(x[a], i, y);
+        const int P = i + H2;
+        in &= (unsigned)P < (unsigned)L.pdims[a];
+        key = key * nb[a] + (P >> lb);
+    });
+    return in ? key : -1;
+}
+
+template <class SP>
+constexpr int box_lb()
+{
+    // bins of 16 cells per axis when the box of every coset fits 96 KB of shared memory, else 8
+    constexpr int w16 = 16 + 2 * SP::HALO + 2;
+    return (SP::M * w16 * w16 * w16 * 4 <= 96 * 1024) ? 4 : 3;
+}
+
+template <class SP>
+constexpr int box_floats()
+{
+    constexpr int W = (1 << box_lb<SP>()) + 2 * SP::HALO + 2;
+    return SP::M * W * W * W;
+}
+
+struct BoxGrid {
+    int nbins;
+    int nb[3];      // bins per axis (bin index = (bx nb1 + by) nb2 + bz)
+    int chunk;      // queries per work item at most
+};
+
+template <class SP>
+__global__ void __launch_bounds__(256, 2) k_adjoint_box(const float4 *__restrict__ q4, const int *__restrict__ bin_start,
+                                                     const int *__restrict__ item_start, BoxGrid g, DevVol<float> v,
+                                                     float *__restrict__ dpad)
+{
+    static_assert(SP::S == 3 && SP::D <= 2, "3-D lattices with coset spacing 1 or 2");
+    constexpr int S = 3, M = SP::M, H = SP::HALO, B = 1 << box_lb<SP>(), W = B + 2 * H + 2, VOL = W * W * W;
+    extern __shared__ float sacc[];
+    const int item = blockIdx.x;
+    if (item >= item_start[g.nbins]) return;
+    int lo = 0, hi = g.nbins - 1;                         // the item's bin: last b with item_start[b] <= item
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (item_start[mid] <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    const int bin = lo;
+    const int q0 = bin_start[bin] + (item - item_start[bin]) * g.chunk;
+    const int q1 = min(q0 + g.chunk, bin_start[bin + 1]);
+    int blo[S];
+    blo[2] = (bin % g.nb[2]) * B - 1 - H;
+    blo[1] = ((bin / g.nb[2]) % g.nb[1]) * B - 1 - H;
+    blo[0] = (bin / (g.nb[2] * g.nb[1])) * B - 1 - H;
+    constexpr int lstride[S] = {W * W, W, 1};
+    for (int i = threadIdx.x; i < M * VOL; i += blockDim.x) sacc[i] = 0.0f;
+    __syncthreads();
+    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+        const float4 r = q4[q];
+        const float x[S] = {r.x, r.y, r.z};
+        const float w = r.w;
+        sfor<M>([&](auto Kc) {
+            constexpr int K = decltype(Kc)::value;
+            const auto f = fold_coset<SP, K, float>(x, v);
+            if (!f.in_range) return;
+            int lbase = K * VOL, lss[S];
+            bool inbox = true;
+            sfor<S>([&](auto A) {
+                constexpr int a = decltype(A)::value;
+                float y;
+                int i;
+                reduce_axis<SP::D, SP::COSET[K][a]>(x[a], i, y);
+                const int lp = i + 2 * H - blo[a];        // box coordinate of the cell's site
+                inbox &= lp >= H && lp < W - H;            // its stencil inside the box
+                lbase += lp * lstride[a];
+                int st = lstride[0];
+                sfor<S - 1>([&](auto Bc) {
+                    if (f.sl[A].ax == 1 + decltype(Bc)::value) st = lstride[1 + decltype(Bc)::value];
+                });
+                lss[A] = f.sl[A].sg * st;
+            });
+            // always inside for a query of this bin (the binning takes the same cell); a query
+            // outside would add straight to the global buffer
+            sfor<SP::K>([&](auto Jc) {
+                if (f.piece == decltype(Jc)::value) {
+                    if (inbox) adjoint_piece_local<SP, decltype(Jc)::value>(f, lss, lbase, sacc, w);
+                    else adjoint_piece<SP, decltype(Jc)::value>(f, dpad, w);
+                }
+            });
+        });
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < M * VOL; i += blockDim.x) {
+        const float a = sacc[i];
+        if (a == 0.0f) continue;
+        const int k = i / VOL;
+        const int r = i - k * VOL;
+        const int p[S] = {blo[0] + r / (W * W), blo[1] + (r / W) % W, blo[2] + r % W};
+        bool in = true;
+        int off = k * v.L.kw;
+        sfor<S>([&](auto A) {
+            constexpr int LB = axis_lb<SP, float>(decltype(A)::value);
+            in &= (unsigned)p[A] < (unsigned)v.L.pdims[A];
+            off += (p[A] >> LB) * v.L.bstride[A] + (p[A] & ((1 << LB) - 1)) * v.L.wt[A];
+        });
+        if (in) atomicAdd(dpad + off, a);
     }
 }
 

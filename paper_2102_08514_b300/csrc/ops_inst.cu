@@ -2,7 +2,6 @@
 // compiles this file once per (spline, family) with -DINTERP_SPLINE=<name> -DINTERP_PART=<0..3>
 // so the large unrolled kernels compile in parallel.
 #include <algorithm>
-#include <cstdlib>
 
 #include "kernels.cuh"
 #include "registry.h"
@@ -79,19 +78,17 @@ constexpr int bin_tile()
 
 template <class CT, int MODE>
 [[maybe_unused]] cudaError_t launch_eval_binned(const float *pts, int64_t n, const void *c, const ibl::Layout &L,
-                                                float *out, float *grad, const float *gout, cudaStream_t st)
+                                                float *out, float *grad, const float *gout, int flags, cudaStream_t st)
 {
     if constexpr (SP::K > 1) {
-        // INTERP_B300_BINCFG=small selects 256-query tiles on 128-thread CTAs (several CTAs per SM)
-        const char *cfg = std::getenv("INTERP_B300_BINCFG");
-        if (cfg && cfg[0] == 's') return launch_binned_cfg<CT, MODE, 256, 128>(pts, n, c, L, out, grad, gout, st);
+        // FLAG_BIN_SMALL: 256-query tiles on 128-thread CTAs (several CTAs per SM)
+        if (flags & ibr::FLAG_BIN_SMALL) return launch_binned_cfg<CT, MODE, 256, 128>(pts, n, c, L, out, grad, gout, st);
         if constexpr (SP::DENSE) {
             // the dense piece tables (one shared code path for all pieces) are slower here than the
             // unrolled per-piece code, whose 1.8x fewer FMAs outweigh its instruction fetch
             // (measured, BCC V_2, 2^24 random queries: value 5.65 vs 8.67 ms, value+grad 6.81 vs
-            // 9.99 ms); INTERP_B300_DENSE=1 selects them
-            const char *dn = std::getenv("INTERP_B300_DENSE");
-            if (dn && dn[0] == '1')
+            // 9.99 ms); FLAG_DENSE_ON selects them
+            if (flags & ibr::FLAG_DENSE_ON)
                 return launch_binned_cfg<CT, MODE, bin_tile<MODE>(), 512, true>(pts, n, c, L, out, grad, gout, st);
         }
         return launch_binned_cfg<CT, MODE, bin_tile<MODE>(), 512>(pts, n, c, L, out, grad, gout, st);
@@ -102,7 +99,7 @@ template <class CT, int MODE>
 
 template <class CT, int MODE>
 cudaError_t launch_eval(const float *pts, int64_t n, const void *c, const ibl::Layout &L, float *out, float *grad,
-                        const float *gout, cudaStream_t st)
+                        const float *gout, int, cudaStream_t st)
 {
     ib::k_eval<SP, CT, MODE><<<grid_for(n), kTPB, 0, st>>>(pts, n, make_vol<CT>(c, L), out, grad, gout);
     return cudaPeekAtLastError();
@@ -141,13 +138,45 @@ cudaError_t launch_eval(const float *pts, int64_t n, const void *c, const ibl::L
     return cudaPeekAtLastError();
 }
 
+[[maybe_unused]] cudaError_t launch_adjoint_box(const ibr::BoxArgs &a, const ibl::Layout &L, float *dpad, cudaStream_t st)
+{
+    if constexpr (SP::S == 3 && SP::K < 4 && SP::D <= 2) {
+        constexpr size_t smem = (size_t)ib::box_floats<SP>() * sizeof(float);
+        static_assert(smem <= kMaxSmem, "adjoint box must fit shared memory");
+        auto kern = ib::k_adjoint_box<SP>;
+        static unsigned long long configured = 0;          // per device: the attribute is set once
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev >= 64 || !(configured >> dev & 1ull)) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            if (dev < 64) configured |= 1ull << dev;
+        }
+        ib::BoxGrid g;
+        g.nbins = a.nbins;
+        g.nb[0] = a.nb[0];
+        g.nb[1] = a.nb[1];
+        g.nb[2] = a.nb[2];
+        g.chunk = a.chunk;
+        kern<<<(unsigned)a.max_items, 256, smem, st>>>(static_cast<const float4 *>(a.q4), a.bin_start, a.item_start, g,
+                                                        make_vol<float>(nullptr, L), dpad);
+        return cudaPeekAtLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
 // counting sort of the queries by Morton-ordered bins: count, exclusive scan, scatter
 [[maybe_unused]] cudaError_t launch_sort(const float *pts, int64_t n, const ibl::Layout &L, int bb, int bits,
                                          unsigned *keys, int nkeys, int32_t *perm, float *pts_out, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(keys, 0, (size_t)nkeys * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
-    const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 148 * 16);
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return cudaGetLastError();
+    const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 16);
     ib::k_sort_count<SP><<<grid, 256, 0, st>>>(pts, n, L, bb, bits, keys);
     // exclusive scan of the counters; the block sums live right after them
     const int nblk = (nkeys + ib::kScanBlock - 1) / ib::kScanBlock;
@@ -168,23 +197,20 @@ cudaError_t launch_eval(const float *pts, int64_t n, const void *c, const ibl::L
 
 template <bool GRAD>
 [[maybe_unused]] cudaError_t launch_rays(const ibl::RayGeom &rg, const void *c, const ibl::Layout &L, float *out,
-                                         float *pts_out, cudaStream_t st)
+                                         float *pts_out, int flags, cudaStream_t st)
 {
     if constexpr (SP::S == 3) {
         if constexpr (SP::K > 1) {
             // multi-piece splines: whole rays per tile, samples binned by piece (as eval_launch:
-            // default for K >= 4, INTERP_B300_BINNED=0 / 1 forces the plain / binned kernel)
+            // default for K >= 4, FLAG_BINNED_OFF / FLAG_BINNED_ON force the plain / binned kernel)
             constexpr int T = bin_tile<GRAD ? 1 : 0>();
-            const char *bn = std::getenv("INTERP_B300_BINNED");
-            const bool want = bn ? bn[0] == '1' : SP::K >= 4;
+            const bool want = (flags & ibr::FLAG_BINNED_ON) ? true : (flags & ibr::FLAG_BINNED_OFF) ? false : SP::K >= 4;
             if (want && rg.steps >= 1 && rg.steps <= T) {
                 constexpr size_t smem = ib::binned_smem_bytes<SP, GRAD ? 1 : 0, T>();
                 static_assert(smem <= kMaxSmem, "binned tile must fit shared memory");
                 // rays of a dense-table spline use the tables (measured, BCC V_2, 1024^2 x 256: value
-                // 127 -> 104 ms, value+grad 151 -> 104 ms); INTERP_B300_DENSE=0 selects the
-                // unrolled code
-                const char *dn = std::getenv("INTERP_B300_DENSE");
-                const bool dense = SP::DENSE && (!dn || dn[0] != '0');
+                // 127 -> 104 ms, value+grad 151 -> 104 ms); FLAG_DENSE_OFF selects the unrolled code
+                const bool dense = SP::DENSE && !(flags & ibr::FLAG_DENSE_OFF);
                 auto kd = ib::k_rays_binned<SP, GRAD, T, 512, SP::DENSE>;
                 auto kp = ib::k_rays_binned<SP, GRAD, T, 512>;
                 auto kern = dense ? kd : kp;
@@ -237,6 +263,10 @@ void IB_CAT(fill_, INTERP_SPLINE, _, INTERP_PART)(SplineOps &o)
     o.fma_grad = SP::FMA_GRAD;
     o.lookups = SP::LOOKUPS;
     o.adjoint = launch_adjoint;
+    if constexpr (SP::S == 3 && SP::K < 4 && SP::D <= 2) {
+        o.adjoint_box = launch_adjoint_box;
+        o.box_lb = ib::box_lb<SP>();
+    }
     o.debug = launch_debug;
     o.sort = launch_sort;
     if constexpr (SP::S == 3) {

@@ -9,13 +9,32 @@
 
 namespace ibr {
 
+// launch options a handle passes to the launchers (set per handle, see interp_set_option)
+enum LaunchFlags : int {
+    FLAG_BIN_SMALL = 1,     // piece-binned kernels: 256-query tiles on 128-thread CTAs
+    FLAG_DENSE_ON = 2,      // dense piece tables where emitted (binned evaluation and rays)
+    FLAG_DENSE_OFF = 4,     // unrolled per-piece code even for the rays of dense-table splines
+    FLAG_BINNED_ON = 8,     // rays: the piece-binned kernel for any multi-piece spline
+    FLAG_BINNED_OFF = 16,   // rays: the plain kernel
+};
+
 using EvalFn = cudaError_t (*)(const float *, int64_t, const void *, const ibl::Layout &, float *, float *,
-                               const float *, cudaStream_t);
+                               const float *, int, cudaStream_t);
 using AdjFn = cudaError_t (*)(const float *, int64_t, const float *, const ibl::Layout &, float *, cudaStream_t);
-using RayFn = cudaError_t (*)(const ibl::RayGeom &, const void *, const ibl::Layout &, float *, float *, cudaStream_t);
+using RayFn = cudaError_t (*)(const ibl::RayGeom &, const void *, const ibl::Layout &, float *, float *, int,
+                              cudaStream_t);
 using SortFn = cudaError_t (*)(const float *, int64_t, const ibl::Layout &, int, int, unsigned *, int, int32_t *,
                                float *, cudaStream_t);
 using DbgFn = cudaError_t (*)(const float *, int64_t, const ibl::Layout &, int32_t *, int32_t *, cudaStream_t);
+// the adjoint on spatially binned queries (x, y, z, gout) per query: (queries, bin starts, work
+// item starts, bins per axis and chunk, padded FP32 layout, gradient buffer, max work items)
+struct BoxArgs {
+    const void *q4;
+    const int *bin_start;
+    const int *item_start;
+    int nbins, nb[3], chunk, max_items;
+};
+using BoxAdjFn = cudaError_t (*)(const BoxArgs &, const ibl::Layout &, float *, cudaStream_t);
 
 struct SplineOps {
     const char *name = nullptr;
@@ -27,6 +46,8 @@ struct SplineOps {
     EvalFn eval[3][3] = {};      // [storage: f32, f16, bf16][mode: value, value+grad, pullback]
     EvalFn eval_binned[3][3] = {};  // the same, piece-binned (multi-piece splines only)
     AdjFn adjoint = nullptr;
+    BoxAdjFn adjoint_box = nullptr;  // 3-D splines with fewer than 4 pieces
+    int box_lb = 0;                  // log2 cells per bin and axis of adjoint_box
     RayFn rays[2] = {};          // [value, value+grad], 3-D splines, FP32 storage
     DbgFn debug = nullptr;
     SortFn sort = nullptr;

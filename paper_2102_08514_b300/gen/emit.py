@@ -76,6 +76,70 @@ def horner_grad_fma_count(s, d):
     return inner + d * (s + 1)
 
 
+def _block_off(nv, d, k):
+    return sum(n_monomials(nv - 1, d - kk) for kk in range(k))
+
+
+def horner_ops(nz, s, d, off=0):
+    """(nonzero?, FP32 operations) of the kernels' nested Horner evaluation of a polynomial in s
+    variables of degree d whose coefficients b[off ..] (nested-Horner layout) are structurally
+    zero outside the index set nz.  A step acc * t + p costs one FMA when both are nonzero, one
+    multiply when only acc is, nothing when acc is zero (acc = p); zero coefficients are never
+    loaded or added."""
+    if s == 0:
+        return off in nz, 0
+    acc, ops = horner_ops(nz, s - 1, 0, off + _block_off(s, d, d))
+    for k in range(d - 1, -1, -1):
+        p, o = horner_ops(nz, s - 1, d - k, off + _block_off(s, d, k))
+        ops += o
+        if acc:
+            ops += 1
+        elif p:
+            acc = True
+    return acc, ops
+
+
+def horner_grad_ops(nz, s, d, off=0):
+    """(value nonzero?, [partials nonzero?], FP32 operations) of the nested Horner evaluation
+    that carries the s partial derivatives, with the same structural-zero rule as horner_ops."""
+    if s == 0:
+        return off in nz, [], 0
+    v, g, ops = horner_grad_ops(nz, s - 1, 0, off + _block_off(s, d, d))
+    g0, gr = False, list(g)
+
+    def step(a, b):
+        # a * t + b: one operation unless a is zero; the result is nonzero if either is
+        return (a or b), (1 if a else 0)
+
+    for k in range(d - 1, -1, -1):
+        pv, pg, o = horner_grad_ops(nz, s - 1, d - k, off + _block_off(s, d, k))
+        ops += o
+        if k == d - 1:
+            g0 = v                                   # d/dt_1 of the leading block: a copy
+        else:
+            g0, o = step(g0, v)
+            ops += o
+        v, o = step(v, pv)
+        ops += o
+        for j in range(s - 1):
+            gr[j], o = step(gr[j], pg[j])
+            ops += o
+    return v, [g0] + gr, ops
+
+
+def op_counts(s, degree, M, pieces):
+    """FP32 operations per query of one value and of one value + gradient evaluation: per coset
+    and piece (weighted by the piece's share of the fold chamber) the nonzeros of A_j (b = A_j c)
+    plus the Horner steps on structurally nonzero data, and the sums over the M cosets.
+    pieces: (volume fraction, [(site, monomial index, value)]) per piece."""
+    val = grad = 0.0
+    for w, z in pieces:
+        nz = {a for _, a, _ in z}
+        val += w * (len(z) + horner_ops(nz, s, degree)[1])
+        grad += w * (len(z) + horner_grad_ops(nz, s, degree)[2])
+    return M * val + (M - 1), M * grad + (M - 1) * (1 + s)
+
+
 def piece_volumes(T):
     from scipy.spatial import ConvexHull
     vols = []
@@ -110,8 +174,7 @@ def emit_struct(T, half_storage: bool = True) -> tuple[str, dict]:
     hv = horner_fma_count(s, T.degree)
     hg = horner_grad_fma_count(s, T.degree)
     M = len(T.cosets)
-    fma_value = M * sum(w * (len(z) + hv) for w, z in zip(vols, nz_lists))
-    fma_grad = M * sum(w * (len(z) + hg) for w, z in zip(vols, nz_lists))
+    fma_value, fma_grad = op_counts(s, T.degree, M, list(zip(vols, nz_lists)))
     lookups = M * sum(w * len(pc.sites) for w, pc in zip(vols, T.pieces))
 
     L = [f"// ---- spline {T.name}"]
@@ -223,13 +286,37 @@ def emit_struct(T, half_storage: bool = True) -> tuple[str, dict]:
     return "\n".join(L), meta
 
 
+def recount(struct_text: str, meta: dict) -> tuple[str, dict]:
+    """A spline's emitted struct and metadata with the operation counts recomputed from the
+    metadata's exact polynomials (the counts are the only change)."""
+    s, deg = meta["s"], meta["degree"]
+    index = {e: i for i, e in enumerate(horner_order(s, deg))}
+    pieces = []
+    for pc in meta["pieces"]:
+        z = [(m, index[tuple(int(v) for v in e.split(","))], Fr(v))
+             for m, P in enumerate(pc["polys"]) for e, v in P.items()]
+        pieces.append((pc["volume_fraction"], z))
+    fv, fg = op_counts(s, deg, len(meta["cosets"]), pieces)
+    meta = dict(meta, fma_value=fv, fma_grad=fg)
+    lines = struct_text.split("\n")
+    for i, ln in enumerate(lines):
+        if "static constexpr double FMA_VALUE" in ln:
+            lookups = ln.split("LOOKUPS = ")[1].rstrip(";")
+            lines[i] = f"    static constexpr double FMA_VALUE = {fv!r}, FMA_GRAD = {fg!r}, LOOKUPS = {lookups};"
+    return "\n".join(lines), meta
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=OUT_DIR)
     ap.add_argument("names", nargs="*", default=list(CATALOG) + list(VORONOI))
     ap.add_argument("--update", nargs="+", default=None, metavar="NAME",
                     help="re-analyse only these splines; take the others from the current output")
+    ap.add_argument("--recount", action="store_true",
+                    help="recompute only the operation counts of the current output (no re-analysis)")
     args = ap.parse_args(argv)
+    if args.recount:
+        args.update = ["__none__"]
     os.makedirs(args.out, exist_ok=True)
     old_structs, old_metas = {}, {}
     if args.update:
@@ -243,8 +330,11 @@ def main(argv=None):
     structs, metas = [], {}
     for name in args.names:
         if args.update and name not in args.update and name in old_structs and name in old_metas:
-            structs.append(old_structs[name])
-            metas[name] = old_metas[name]
+            st, meta = old_structs[name], old_metas[name]
+            if args.recount:
+                st, meta = recount(st, meta)
+            structs.append(st)
+            metas[name] = meta
             continue
         T = analyse_entry(name)
         if len(T.pieces) > MAX_PIECES or len(T.planes) > MAX_Q:

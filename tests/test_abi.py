@@ -63,3 +63,12 @@ def test_create_argument_errors_without_gpu(lib):
     assert e.value.status == binding.INTERP_EUNSUPPORTED
     h = binding.load()
     assert h.interp_eval(None, None, 0, None, None) == binding.INTERP_EINVAL
+
+
+def test_option_argument_errors_without_gpu(lib):
+    from paper_2102_08514_b300 import binding
+    h = binding.load()
+    assert h.interp_set_option(None, b"binned", 1) == binding.INTERP_EINVAL
+    v = ctypes.c_int()
+    assert h.interp_get_option(None, b"presort", ctypes.byref(v)) == binding.INTERP_EINVAL
+    assert h.interp_debug_device_allocations() >= 0

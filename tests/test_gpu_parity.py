@@ -125,7 +125,7 @@ def test_adjoint_parity(name):
 
 
 @pytest.mark.parametrize("name", ["bcc_linear", "cc_linear_rd", "cc_voronoi1", "bcc_voronoi1", "fcc_voronoi1"])
-def test_gradient_at_exact_ties(name, monkeypatch):
+def test_gradient_at_exact_ties(name):
     # continuous, not C^1 splines: at points exactly on mesh planes (integer, half and quarter
     # coordinates, and sums of them) the gradient is the one-sided limit along the fixed world
     # direction v = (1, 2^-12, 2^-24), on the GPU (every coset and fold decision) as in the oracle
@@ -141,7 +141,7 @@ def test_gradient_at_exact_ties(name, monkeypatch):
     pts[::3, 1] = (np.round(rng.uniform(lo[1], hi[1], 500) * 2 ** 12) / 2 ** 12).astype(np.float32)
     pts[1::3, 0] = (np.floor(pts[1::3, 1]) + 0.5 - (pts[1::3, 1] - np.floor(pts[1::3, 1]))).astype(np.float32)
     for flag in ("1", "0") if SPLINES[name].order else ("0",):
-        monkeypatch.setenv("INTERP_B300_BINNED", flag)         # binned and plain kernels alike
+        itp.set_option("binned", int(flag))         # binned and plain kernels alike
         val, grad = itp.eval_grad(torch.from_numpy(pts).cuda())
         ref_v, ref_g = OracleSpline(name).eval_sum(lat.D, lat.cosets, c, pts, grad=True)
         cmax = np.abs(c).max()
@@ -260,9 +260,9 @@ def test_full_size_headline_workload_sampled():
 
 
 @pytest.mark.parametrize("name", ["fcc_6dir", "d4s_8dir", "d4_8dir", "bcc_voronoi1", "fcc_voronoi2", "bcc_voronoi2"])
-def test_piece_binned_kernel_equals_plain_kernel(name, monkeypatch):
-    # multi-piece splines run a piece-binned kernel by default; INTERP_B300_BINNED=0 selects the
-    # plain one: same sums in the same order, so the results agree exactly
+def test_piece_binned_kernel_equals_plain_kernel(name):
+    # multi-piece splines run a piece-binned kernel by default; the handle option "binned" = 0
+    # selects the plain one: same sums in the same order, so the results agree exactly
     n_axis, nq = SMALL[name]
     sp, lat, xi, detl = spline_setup(name)
     dims = (n_axis,) * xi.shape[0]
@@ -273,7 +273,7 @@ def test_piece_binned_kernel_equals_plain_kernel(name, monkeypatch):
     from paper_2102_08514_b300.binding import interp_backward
     res = []
     for flag in ("1", "0"):
-        monkeypatch.setenv("INTERP_B300_BINNED", flag)
+        itp.set_option("binned", int(flag))
         v = itp.eval(pts)
         v2, gr = itp.eval_grad(pts)
         dp = torch.empty_like(gr)

@@ -4,7 +4,7 @@ calls of 2^16 or more queries sort the queries on the device by the pieces of th
 results to the callers' positions.  A query's sum does not depend on its tile's other queries, so
 values, gradients and pullbacks equal the unsorted binned kernel's bit for bit; the adjoint's
 atomic scatter agrees within rounding; under stream capture the call runs unsorted.
-INTERP_B300_PRESORT=0 / 1 forces the pre-sort off / on."""
+The handle option "presort" (0 / 1) forces the pre-sort off / on."""
 import numpy as np
 import pytest
 
@@ -40,7 +40,7 @@ def _run_all(torch, itp, pts, g):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-def test_presorted_equals_unsorted(name, monkeypatch):
+def test_presorted_equals_unsorted(name):
     # fcc_voronoi2 and bcc_voronoi1 do not take the pre-sort by default; forced, it must still agree
     n_axis, n = CASES[name]
     torch, itp, dims, _ = _setup(name, n_axis, 71)
@@ -49,7 +49,7 @@ def test_presorted_equals_unsorted(name, monkeypatch):
     g = torch.linspace(-1, 1, n, device="cuda")
     res = []
     for flag in ("1", "0"):
-        monkeypatch.setenv("INTERP_B300_PRESORT", flag)
+        itp.set_option("presort", int(flag))
         res.append(_run_all(torch, itp, pts, g))
     for a, b in zip(*res):
         assert torch.equal(torch.nan_to_num(a, nan=7.0), torch.nan_to_num(b, nan=7.0))
@@ -57,7 +57,7 @@ def test_presorted_equals_unsorted(name, monkeypatch):
 
 
 @pytest.mark.parametrize("name", ["bcc_voronoi2", "d4s_8dir"])
-def test_presorted_adjoint(name, monkeypatch):
+def test_presorted_adjoint(name):
     n_axis, _ = CASES[name]
     torch, itp, dims, _ = _setup(name, n_axis, 73)
     n = 100_003
@@ -65,7 +65,7 @@ def test_presorted_adjoint(name, monkeypatch):
     g = torch.from_numpy(make_rng(75, 0).uniform(-1, 1, n).astype(np.float32)).cuda()
     out = []
     for flag in ("1", "0"):
-        monkeypatch.setenv("INTERP_B300_PRESORT", flag)
+        itp.set_option("presort", int(flag))
         dc, _ = itp.backward(pts, g)
         torch.cuda.synchronize()
         out.append(dc.clone())
@@ -76,13 +76,13 @@ def test_presorted_adjoint(name, monkeypatch):
     assert (out[0] - out[1]).abs().max().item() <= 1e-4 * scale
 
 
-def test_presorted_matches_oracle(monkeypatch):
+def test_presorted_matches_oracle():
     # the forced pre-sort on a small BCC V_2 case, against the FP64 oracle
     name = "bcc_voronoi2"
     torch, itp, dims, c = _setup(name, 10, 76)
     lat = LATTICES[SPLINES[name].lattice]
     pts = mixed_points(name, dims, 397, 77)
-    monkeypatch.setenv("INTERP_B300_PRESORT", "1")
+    itp.set_option("presort", 1)
     v, gr = itp.eval_grad(torch.from_numpy(pts).cuda())
     ref_v, ref_g = OracleSpline(name).eval_sum(lat.D, lat.cosets, c.astype(np.float64), pts.astype(np.float64),
                                                grad=True)
@@ -143,7 +143,7 @@ def test_presort_default_rule():
         assert itp.info.presort == w, name
 
 
-def test_presorted_half_storage(monkeypatch):
+def test_presorted_half_storage():
     # the pre-sort in front of the FP16-storage binned kernel (BCC V_1 keeps FP16 kernels)
     name = "bcc_voronoi1"
     torch = require_cuda()
@@ -155,7 +155,7 @@ def test_presorted_half_storage(monkeypatch):
     pts = torch.from_numpy(mixed_points(name, dims, 70001, 83)).cuda()
     res = []
     for flag in ("1", "0"):
-        monkeypatch.setenv("INTERP_B300_PRESORT", flag)
+        itp.set_option("presort", int(flag))
         res.append(itp.eval_grad(pts))
     for a, b in zip(*res):
         assert torch.equal(torch.nan_to_num(a, nan=7.0), torch.nan_to_num(b, nan=7.0))

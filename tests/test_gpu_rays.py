@@ -66,9 +66,9 @@ def test_rays_match_oracle(name, grad):
 
 
 @pytest.mark.parametrize("name,steps", [("bcc_voronoi1", 48), ("fcc_voronoi2", 48), ("bcc_voronoi2", 700)])
-def test_binned_rays_equal_plain_rays(name, steps, monkeypatch):
+def test_binned_rays_equal_plain_rays(name, steps):
     # multi-piece splines march rays with the piece-binned kernel (whole rays per tile, sums in
-    # step and coset order); INTERP_B300_BINNED=0 selects the plain kernel: identical sums
+    # step and coset order); the handle option "binned" = 0 selects the plain kernel: identical sums
     torch = require_cuda()
     from paper_2102_08514_b300.binding import interp_eval_rays, make_rays
     dims = (12, 13, 11)
@@ -80,7 +80,7 @@ def test_binned_rays_equal_plain_rays(name, steps, monkeypatch):
     rays = make_rays(origin, du, dv, setup["d"], setup["lo"], setup["hi"], W, H, steps)
     res = []
     for flag in ("1", "0"):
-        monkeypatch.setenv("INTERP_B300_BINNED", flag)
+        itp.set_option("binned", int(flag))
         for grad in (False, True):
             out = torch.full((W * H * (4 if grad else 1),), 7.0, device="cuda")
             pts = torch.empty(W * H * steps * 3, device="cuda")

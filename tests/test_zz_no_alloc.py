@@ -52,6 +52,51 @@ def test_noalloc_adjoint_matches_interp_backward_twice(name, dims):
         assert torch.equal(dpts, dref)
 
 
+@pytest.mark.parametrize("presort", [-1, 1])
+def test_noalloc_allocates_nothing_where_the_pullback_would_presort(presort):
+    """BCC V_2 with 2^16 queries and dpts: interp_backward takes the piece pre-sort there (pool
+    scratch), interp_backward_noalloc must not -- checked with the library's own allocation count,
+    with the default options and with the pre-sort forced on for every call."""
+    import torch
+    from paper_2102_08514_b300.binding import (Interpolator, interp_backward, interp_backward_noalloc,
+                                               interp_debug_device_allocations)
+    name, dims = "bcc_voronoi2", (20, 20, 20)
+    itp = Interpolator.named(name, dims)
+    itp.set_option("presort", presort)
+    itp.set_coeffs(torch.from_numpy(make_rng(7, 1).uniform(-1, 1, itp.shape).astype(np.float32)).cuda())
+    n = 1 << 16
+    pts, g = _case(torch, itp, name, dims, 8, n)
+    ref = torch.zeros(itp.shape, device="cuda")
+    dref = torch.empty(n, 3, device="cuda")
+    interp_backward(itp.handle, pts, g, ref, dref)            # allocates its buffer and pool scratch
+    bound = torch.zeros(itp.shape, device="cuda")
+    interp_backward(itp.handle, pts, g.abs(), bound)
+    got = torch.zeros(itp.shape, device="cuda")
+    dpts = torch.empty(n, 3, device="cuda")
+    torch.cuda.synchronize()
+    for _ in range(2):
+        got.zero_()
+        before = interp_debug_device_allocations()
+        interp_backward_noalloc(itp.handle, pts, g, got, dpts)
+        after = interp_debug_device_allocations()
+        torch.cuda.synchronize()
+        assert after == before
+        assert bool(torch.all((got - ref).abs() <= 4e-6 * bound + 1e-7)), float((got - ref).abs().max())
+        assert torch.equal(dpts, dref)
+
+
+def test_noalloc_dpts_only_has_no_size_limit():
+    from paper_2102_08514_b300.binding import interp_backward, interp_backward_noalloc
+    torch, itp = _setup("cc_7dir", (208, 208, 208), 5)        # padded FP32 buffer > 8 Mi elements
+    pts, g = _case(torch, itp, "cc_7dir", (208, 208, 208), 6, 1000)
+    dpts = torch.empty(1000, 3, device="cuda")
+    interp_backward_noalloc(itp.handle, pts, g, None, dpts)
+    dref = torch.empty_like(dpts)
+    interp_backward(itp.handle, pts, g, None, dref)
+    torch.cuda.synchronize()
+    assert torch.equal(dpts, dref)
+
+
 def test_noalloc_refuses_handles_beyond_its_array():
     from paper_2102_08514_b300.binding import INTERP_ESIZE, InterpError, interp_backward_noalloc
     torch, itp = _setup("cc_7dir", (208, 208, 208), 5)        # padded FP32 buffer > 8 Mi elements
