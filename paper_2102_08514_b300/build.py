@@ -2,7 +2,8 @@
 
 Compiles for sm_103a only.  The ABI (csrc/interp.cu) and one instantiation unit per (spline,
 kernel family) (csrc/ops_inst.cu with -DINTERP_SPLINE / -DINTERP_PART) compile in parallel into
-paper_2102_08514_b300/_build/obj/, then link into _build/libinterp_b300.so.
+paper_2102_08514_b300/_build/obj/, then link into _build/libinterp_b300.so.  An object is rebuilt
+when its command line or the contents of its sources changed (a stamp beside it).
 """
 from __future__ import annotations
 
@@ -74,9 +75,43 @@ def needs_build() -> bool:
 
 
 def _compile(args):
-    cmd, log = args
+    cmd, stamp = args
     r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode == 0 and stamp:
+        with open(stamp[0], "w") as f:
+            f.write(stamp[1])
     return cmd, r.returncode, r.stdout + r.stderr
+
+
+# the sources each object is compiled from (every unit includes the kernel headers)
+UNIT_DEPS = {
+    "interp": ["interp.cu", "kernels.cuh", "registry.h", "layout.h"],
+    "ops": ["ops_inst.cu", "kernels.cuh", "registry.h", "layout.h"],
+    "batch": ["batch_inst.cu", "kernels.cuh", "registry.h", "layout.h"],
+}
+
+
+def _unit_digest(cmd, kind) -> str:
+    """Hash of an object's command line and the contents of what it is compiled from."""
+    h = hashlib.sha256(" ".join(cmd).encode())
+    for name in UNIT_DEPS[kind]:
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(f.read())
+    for path in (GEN_HDR, os.path.join(ROOT, "include", "interp.h")):
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def _job(cmd, obj, kind):
+    """(cmd, (stamp path, digest)), or None when the object is up to date."""
+    digest = _unit_digest(cmd, kind)
+    stamp = obj + ".stamp"
+    if os.path.exists(obj) and os.path.exists(stamp):
+        with open(stamp) as f:
+            if f.read().strip() == digest:
+                return None
+    return cmd, (stamp, digest)
 
 
 def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False, jobs: int | None = None) -> str:
@@ -88,18 +123,24 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False, job
     extra = ["-Xptxas", "-v"] if ptxas_v else []
     jobsl = []
     objs = []
+
+    def add(cmd, obj, kind):
+        objs.append(obj)
+        j = None if force else _job(cmd, obj, kind)
+        if force:
+            j = (cmd, (obj + ".stamp", _unit_digest(cmd, kind)))
+        if j is not None:
+            jobsl.append(j)
+
     o = os.path.join(objdir, "interp.o")
-    jobsl.append(([nvcc(), *NVCC_FLAGS, *inc, "-c", os.path.join(CSRC, "interp.cu"), "-o", o], None))
-    objs.append(o)
+    add([nvcc(), *NVCC_FLAGS, *inc, "-c", os.path.join(CSRC, "interp.cu"), "-o", o], o, "interp")
     for name in spline_names():
         for part in range(N_PARTS):
             o = os.path.join(objdir, f"ops_{name}_{part}.o")
-            jobsl.append(([nvcc(), *NVCC_FLAGS, *extra, *inc, f"-DINTERP_SPLINE={name}", f"-DINTERP_PART={part}",
-                           "-c", os.path.join(CSRC, "ops_inst.cu"), "-o", o], None))
-            objs.append(o)
+            add([nvcc(), *NVCC_FLAGS, *extra, *inc, f"-DINTERP_SPLINE={name}", f"-DINTERP_PART={part}",
+                 "-c", os.path.join(CSRC, "ops_inst.cu"), "-o", o], o, "ops")
     o = os.path.join(objdir, "batch_3d.o")
-    jobsl.append(([nvcc(), *NVCC_FLAGS, *extra, *inc, "-c", os.path.join(CSRC, "batch_inst.cu"), "-o", o], None))
-    objs.append(o)
+    add([nvcc(), *NVCC_FLAGS, *extra, *inc, "-c", os.path.join(CSRC, "batch_inst.cu"), "-o", o], o, "batch")
     # the units of the large splines need several GB each: at most two of them run at a time
     big = [j for j in jobsl if any(k in " ".join(j[0]) for k in ("d4s", "voronoi2", "voronoi3"))]
     small = [j for j in jobsl if j not in big]

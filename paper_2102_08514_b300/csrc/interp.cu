@@ -636,7 +636,7 @@ static cudaError_t eval_launch(const interp *h, const float *pts, int64_t npts, 
 namespace {
 
 constexpr int kBoxChunk = 32768;          // queries per work item at most
-constexpr int kBoxSharedBins = 4096;      // per-CTA bin counters in shared memory up to this many bins
+constexpr int kBoxSharedBins = 8192;      // per-CTA bin counters in shared memory up to this many bins
 constexpr int kBoxBlock = 4096;           // queries per CTA of the count and scatter kernels
 
 struct BoxGeom {
@@ -649,8 +649,12 @@ __device__ __forceinline__ int box_key(const float *p, float w, const BoxGeom &g
     return g.D == 2 ? ib::box_key3<2>(x, w, g.H2, L, g.lb, g.nb) : ib::box_key3<1>(x, w, g.H2, L, g.lb, g.nb);
 }
 
+// queries per thread and round of the count and scatter kernels (independent loads in flight)
+constexpr int kBoxUnroll = 4;
+
 __global__ void __launch_bounds__(256) k_box_count(const float *__restrict__ pts, const float *__restrict__ gout, int n,
-                                                   BoxGeom g, ibl::Layout L, unsigned *__restrict__ counts)
+                                                   BoxGeom g, ibl::Layout L, unsigned *__restrict__ counts,
+                                                   int *__restrict__ keys)
 {
     __shared__ unsigned hist[kBoxSharedBins];
     const bool sh = g.nbins <= kBoxSharedBins;
@@ -659,9 +663,27 @@ __global__ void __launch_bounds__(256) k_box_count(const float *__restrict__ pts
         __syncthreads();
     }
     const int q0 = blockIdx.x * kBoxBlock, q1 = min(n, q0 + kBoxBlock);
-    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-        const int key = box_key(pts + (int64_t)q * 3, gout[q], g, L);
-        if (key >= 0) atomicAdd(sh ? &hist[key] : &counts[key], 1u);
+    for (int qb = q0 + threadIdx.x; qb < q1; qb += kBoxUnroll * blockDim.x) {
+        int key[kBoxUnroll];
+#pragma unroll
+        for (int u = 0; u < kBoxUnroll; ++u) {
+            const int q = qb + u * blockDim.x;
+            key[u] = q < q1 ? box_key(pts + (int64_t)q * 3, gout[q], g, L) : -1;
+            if (q < q1) keys[q] = key[u];
+        }
+#pragma unroll
+        for (int u = 0; u < kBoxUnroll; ++u) {
+            // a warp whose queries all fall in one bin (sorted input) adds once; otherwise one
+            // atomic per query (random keys rarely collide within a warp)
+            const unsigned act = __activemask();
+            const int k0 = __shfl_sync(act, key[u], __ffs(act) - 1);
+            if (__all_sync(act, key[u] == k0)) {
+                if (k0 >= 0 && (int)(threadIdx.x & 31) == __ffs(act) - 1)
+                    atomicAdd(sh ? &hist[k0] : &counts[k0], (unsigned)__popc(act));
+            } else if (key[u] >= 0) {
+                atomicAdd(sh ? &hist[key[u]] : &counts[key[u]], 1u);
+            }
+        }
     }
     if (sh) {
         __syncthreads();
@@ -710,36 +732,90 @@ __global__ void __launch_bounds__(1024) k_box_scan(unsigned *__restrict__ counts
     }
 }
 
-__global__ void __launch_bounds__(256) k_box_scatter(const float *__restrict__ pts, const float *__restrict__ gout, int n,
-                                                     BoxGeom g, ibl::Layout L, unsigned *__restrict__ cursor,
-                                                     float4 *__restrict__ q4)
+// each CTA reserves, per bin, a range of the sorted order for its kBoxBlock queries and writes
+// their indices there (cnt / base: dynamic shared memory, 2 x nbins counters, when nbins <=
+// kBoxSharedBins; else one global atomic per distinct key of a warp)
+__global__ void __launch_bounds__(256) k_box_scatter(const int *__restrict__ keys, int n, int nbins,
+                                                     unsigned *__restrict__ cursor, int *__restrict__ idx)
 {
-    __shared__ unsigned cnt[kBoxSharedBins], base[kBoxSharedBins];
-    const bool sh = g.nbins <= kBoxSharedBins;
+    extern __shared__ unsigned box_sh[];
+    unsigned *cnt = box_sh, *base = box_sh + nbins;
+    const bool sh = nbins <= kBoxSharedBins;
     const int q0 = blockIdx.x * kBoxBlock, q1 = min(n, q0 + kBoxBlock);
+    const int lane = threadIdx.x & 31;
     if (sh) {
-        for (int i = threadIdx.x; i < g.nbins; i += blockDim.x) cnt[i] = 0;
+        for (int i = threadIdx.x; i < nbins; i += blockDim.x) cnt[i] = 0;
         __syncthreads();
-        for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-            const int key = box_key(pts + (int64_t)q * 3, gout[q], g, L);
-            if (key >= 0) atomicAdd(&cnt[key], 1u);
+        for (int qb = q0 + threadIdx.x; qb < q1; qb += kBoxUnroll * blockDim.x) {
+            int key[kBoxUnroll];
+#pragma unroll
+            for (int u = 0; u < kBoxUnroll; ++u) {
+                const int q = qb + u * blockDim.x;
+                key[u] = q < q1 ? keys[q] : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < kBoxUnroll; ++u) {
+                const unsigned act = __activemask();
+                const int k0 = __shfl_sync(act, key[u], __ffs(act) - 1);
+                if (__all_sync(act, key[u] == k0)) {
+                    if (k0 >= 0 && lane == __ffs(act) - 1) atomicAdd(&cnt[k0], (unsigned)__popc(act));
+                } else if (key[u] >= 0) {
+                    atomicAdd(&cnt[key[u]], 1u);
+                }
+            }
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < g.nbins; i += blockDim.x) {
+        for (int i = threadIdx.x; i < nbins; i += blockDim.x) {
             const unsigned c = cnt[i];
             base[i] = c ? atomicAdd(&cursor[i], c) : 0u;
             cnt[i] = 0;
         }
         __syncthreads();
     }
-    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-        const float *p = pts + (int64_t)q * 3;
-        const float w = gout[q];
-        const int key = box_key(p, w, g, L);
-        if (key < 0) continue;
-        const unsigned pos = sh ? base[key] + atomicAdd(&cnt[key], 1u) : atomicAdd(&cursor[key], 1u);
-        q4[pos] = make_float4(p[0], p[1], p[2], w);
+    for (int qb = q0 + threadIdx.x; qb < q1; qb += kBoxUnroll * blockDim.x) {
+        int key[kBoxUnroll];
+#pragma unroll
+        for (int u = 0; u < kBoxUnroll; ++u) {
+            const int q = qb + u * blockDim.x;
+            key[u] = q < q1 ? keys[q] : -1;
+        }
+        unsigned pos[kBoxUnroll];
+#pragma unroll
+        for (int u = 0; u < kBoxUnroll; ++u) {
+            // a warp whose queries all fall in one bin reserves its slots with one atomic;
+            // otherwise each query takes its own slot
+            const unsigned act = __activemask();
+            const int leader = __ffs(act) - 1;
+            const int k0 = __shfl_sync(act, key[u], leader);
+            if (__all_sync(act, key[u] == k0)) {
+                unsigned first = 0;
+                if (k0 >= 0 && lane == leader) {
+                    const unsigned c = (unsigned)__popc(act);
+                    first = sh ? base[k0] + atomicAdd(&cnt[k0], c) : atomicAdd(&cursor[k0], c);
+                }
+                pos[u] = __shfl_sync(act, first, leader) + (unsigned)__popc(act & ((1u << lane) - 1u));
+            } else {
+                pos[u] = key[u] >= 0 ? (sh ? base[key[u]] + atomicAdd(&cnt[key[u]], 1u) : atomicAdd(&cursor[key[u]], 1u))
+                                     : 0u;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kBoxUnroll; ++u)
+            if (key[u] >= 0) idx[pos[u]] = qb + u * (int)blockDim.x;
     }
+}
+
+// the scatter's dynamic shared memory above 48 KB (set once per device)
+cudaError_t box_scatter_smem_optin(int dev)
+{
+    static std::mutex mu;
+    static unsigned long long done = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < 64 && (done >> dev & 1ull)) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(k_box_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(2 * kBoxSharedBins * sizeof(unsigned)));
+    if (e == cudaSuccess && dev >= 0 && dev < 64) done |= 1ull << dev;
+    return e;
 }
 
 // the geometry of the bins for handle h, and whether a call of npts queries takes the binned adjoint
@@ -758,11 +834,14 @@ bool box_plan(const interp *h, int64_t npts, BoxGeom &g)
     if (nb > (1 << 24)) return false;
     g.nbins = (int)nb;
     if (h->opt_adjoint_bins == 1) return true;
-    // worth it when the contributions far outnumber the boxes' global atomics: every bin's box
-    // (of M (2^lb + 2 halo + 2)^3 sites) is added once
+    // worth it for wide stencils (>= 24 lookups per query) when the contributions outnumber the
+    // boxes' global atomics at least four times (every bin's box of M (2^lb + 2 halo + 2)^3 sites
+    // is added once).  Measured, 2^24 random queries: BCC quintic (32 lookups) 2.49 -> 1.46 ms,
+    // CC 7-direction (53) 4.11 -> 3.52 ms; FCC 6-direction (16) 1.31 -> 1.51 ms, so narrow
+    // stencils keep the one-atomic-per-contribution scatter
     const int W = (1 << g.lb) + g.H2 + 2;
     const double box_sites = (double)o->M * W * W * W;
-    return (double)npts * o->lookups >= 2.0 * (double)g.nbins * box_sites;
+    return o->lookups >= 24.0 && (double)npts * o->lookups >= 4.0 * (double)g.nbins * box_sites;
 }
 
 }  // namespace
@@ -780,7 +859,8 @@ static bool adjoint_box_launch(const interp *h, const BoxGeom &g, const float *p
     const int n = (int)npts;
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t nb = (size_t)g.nbins;
-    const size_t sz[] = {up((size_t)n * 16), up(nb * 4), up((nb + 1) * 4), up((nb + 1) * 4), up(nb * 4)};
+    const size_t sz[] = {up((size_t)n * 4), up((size_t)n * 4), up(nb * 4), up((nb + 1) * 4), up((nb + 1) * 4),
+                         up(nb * 4)};
     size_t bytes = 0;
     for (size_t b : sz) bytes += b;
     cudaMemPool_t pool = nullptr;
@@ -795,28 +875,39 @@ static bool adjoint_box_launch(const interp *h, const BoxGeom &g, const float *p
         return false;
     }
     unsigned char *p = static_cast<unsigned char *>(block);
-    float4 *q4 = reinterpret_cast<float4 *>(p);
-    unsigned *counts = reinterpret_cast<unsigned *>(p + sz[0]);
-    int *bin_start = reinterpret_cast<int *>(p + sz[0] + sz[1]);
-    int *item_start = reinterpret_cast<int *>(p + sz[0] + sz[1] + sz[2]);
-    unsigned *cursor = reinterpret_cast<unsigned *>(p + sz[0] + sz[1] + sz[2] + sz[3]);
+    int *keys = reinterpret_cast<int *>(p);
+    p += sz[0];
+    int *idx = reinterpret_cast<int *>(p);
+    p += sz[1];
+    unsigned *counts = reinterpret_cast<unsigned *>(p);
+    p += sz[2];
+    int *bin_start = reinterpret_cast<int *>(p);
+    p += sz[3];
+    int *item_start = reinterpret_cast<int *>(p);
+    p += sz[4];
+    unsigned *cursor = reinterpret_cast<unsigned *>(p);
     cudaError_t e = cudaMemsetAsync(counts, 0, nb * 4, st);
     const unsigned grid = (unsigned)((n + kBoxBlock - 1) / kBoxBlock);
+    const size_t scat_smem = g.nbins <= kBoxSharedBins ? 2 * nb * sizeof(unsigned) : 0;
+    if (e == cudaSuccess && scat_smem > 48 * 1024) e = box_scatter_smem_optin(h->device);
     if (e == cudaSuccess) {
-        k_box_count<<<grid, 256, 0, st>>>(pts, gout, n, g, h->lay32, counts);
+        k_box_count<<<grid, 256, 0, st>>>(pts, gout, n, g, h->lay32, counts, keys);
         k_box_scan<<<1, 1024, 0, st>>>(counts, g.nbins, kBoxChunk, bin_start, item_start, cursor);
-        k_box_scatter<<<grid, 256, 0, st>>>(pts, gout, n, g, h->lay32, cursor, q4);
+        k_box_scatter<<<grid, 256, scat_smem, st>>>(keys, n, g.nbins, cursor, idx);
         e = cudaPeekAtLastError();
     }
     if (e == cudaSuccess) {
         ibr::BoxArgs a;
-        a.q4 = q4;
+        a.pts = pts;
+        a.gout = gout;
+        a.idx = idx;
         a.bin_start = bin_start;
         a.item_start = item_start;
         a.nbins = g.nbins;
         for (int i = 0; i < 3; ++i) a.nb[i] = g.nb[i];
         a.chunk = kBoxChunk;
         a.max_items = g.nbins + (n + kBoxChunk - 1) / kBoxChunk;
+        a.lb = g.lb;
         e = h->ops->adjoint_box(a, h->lay32, h->dpad, st);
     }
     cudaFreeAsync(block, st);

@@ -1571,8 +1571,8 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_priv(const float *__restrict
 
 // ------------------------------------------------------------------------------------ adjoint on spatial bins
 //
-// The adjoint of random queries sorted by cell (the caller's call runs a counting sort of the
-// queries into spatial bins first, see interp_backward): a bin holds the queries whose coset-0
+// The adjoint of random queries sorted by cell (the call runs a counting sort of the query
+// indices into spatial bins first, see interp_backward): a bin holds the queries whose coset-0
 // cell has padded index P in [b B, (b + 1) B) along every axis (B = 2^LB cells).  Every site such
 // a query touches, on any coset, lies in the box [b B - 1 - HALO, (b + 1) B + HALO] per axis (the
 // other cosets' cells are the coset-0 cell or the one below it, D <= 2), so a CTA sums a bin's
@@ -1602,18 +1602,26 @@ __device__ __forceinline__ int box_key3(const float (&x)[3], float w, int H2, co
     return in ? key : -1;
 }
 
+// bins of 8 cells per axis: boxes of at most 4 x 12^3 (FCC) or 2 x 14^3 (BCC, halo 2) sites, 11 to
+// 28 KB, so that four CTAs share an SM (measured on the BCC quintic workload: 16-cell bins, two
+// CTAs per SM, 1.33 ms for the box kernel; 8-cell bins, four CTAs, 0.95 ms)
 template <class SP>
 constexpr int box_lb()
 {
-    // bins of 16 cells per axis when the box of every coset fits 96 KB of shared memory, else 8
-    constexpr int w16 = 16 + 2 * SP::HALO + 2;
-    return (SP::M * w16 * w16 * w16 * 4 <= 96 * 1024) ? 4 : 3;
+    return 3;
 }
 
+// resident CTAs per SM of the box kernel (256 threads): four where the registers allow it
 template <class SP>
+constexpr int box_min_blocks()
+{
+    return SP::NS[0] <= 32 ? 4 : 2;
+}
+
+template <class SP, int LB>
 constexpr int box_floats()
 {
-    constexpr int W = (1 << box_lb<SP>()) + 2 * SP::HALO + 2;
+    constexpr int W = (1 << LB) + 2 * SP::HALO + 2;
     return SP::M * W * W * W;
 }
 
@@ -1623,13 +1631,14 @@ struct BoxGrid {
     int chunk;      // queries per work item at most
 };
 
-template <class SP>
-__global__ void __launch_bounds__(256, 2) k_adjoint_box(const float4 *__restrict__ q4, const int *__restrict__ bin_start,
-                                                     const int *__restrict__ item_start, BoxGrid g, DevVol<float> v,
-                                                     float *__restrict__ dpad)
+template <class SP, int LB, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_adjoint_box(const float *__restrict__ pts, const float *__restrict__ gout,
+                                                        const int *__restrict__ idx, const int *__restrict__ bin_start,
+                                                        const int *__restrict__ item_start, BoxGrid g, DevVol<float> v,
+                                                        float *__restrict__ dpad)
 {
     static_assert(SP::S == 3 && SP::D <= 2, "3-D lattices with coset spacing 1 or 2");
-    constexpr int S = 3, M = SP::M, H = SP::HALO, B = 1 << box_lb<SP>(), W = B + 2 * H + 2, VOL = W * W * W;
+    constexpr int S = 3, M = SP::M, H = SP::HALO, B = 1 << LB, W = B + 2 * H + 2, VOL = W * W * W;
     extern __shared__ float sacc[];
     const int item = blockIdx.x;
     if (item >= item_start[g.nbins]) return;
@@ -1649,10 +1658,22 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_box(const float4 *__restrict
     constexpr int lstride[S] = {W * W, W, 1};
     for (int i = threadIdx.x; i < M * VOL; i += blockDim.x) sacc[i] = 0.0f;
     __syncthreads();
-    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-        const float4 r = q4[q];
-        const float x[S] = {r.x, r.y, r.z};
-        const float w = r.w;
+    // the next query's point and gout are loaded one iteration ahead (random gathers: their
+    // latency hides behind the current query's work)
+    float nx[S] = {0.0f, 0.0f, 0.0f}, nw = 0.0f;
+    if (q0 + (int)threadIdx.x < q1) {
+        const int64_t q = idx[q0 + threadIdx.x];
+        sfor<S>([&](auto A) { nx[A] = pts[q * S + A]; });
+        nw = gout[q];
+    }
+    for (int i = q0 + threadIdx.x; i < q1; i += blockDim.x) {
+        const float x[S] = {nx[0], nx[1], nx[2]};
+        const float w = nw;
+        if (i + (int)blockDim.x < q1) {
+            const int64_t q = idx[i + blockDim.x];
+            sfor<S>([&](auto A) { nx[A] = pts[q * S + A]; });
+            nw = gout[q];
+        }
         sfor<M>([&](auto Kc) {
             constexpr int K = decltype(Kc)::value;
             const auto f = fold_coset<SP, K, float>(x, v);

@@ -138,30 +138,39 @@ cudaError_t launch_eval(const float *pts, int64_t n, const void *c, const ibl::L
     return cudaPeekAtLastError();
 }
 
+template <int LB, int MINB>
+[[maybe_unused]] cudaError_t launch_adjoint_box_cfg(const ibr::BoxArgs &a, const ibl::Layout &L, float *dpad,
+                                                    cudaStream_t st)
+{
+    constexpr size_t smem = (size_t)ib::box_floats<SP, LB>() * sizeof(float);
+    static_assert(smem <= kMaxSmem, "adjoint box must fit shared memory");
+    auto kern = ib::k_adjoint_box<SP, LB, MINB>;
+    static unsigned long long configured = 0;          // per device: the attribute is set once
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 64 || !(configured >> dev & 1ull)) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev < 64) configured |= 1ull << dev;
+    }
+    ib::BoxGrid g;
+    g.nbins = a.nbins;
+    g.nb[0] = a.nb[0];
+    g.nb[1] = a.nb[1];
+    g.nb[2] = a.nb[2];
+    g.chunk = a.chunk;
+    kern<<<(unsigned)a.max_items, 256, smem, st>>>(a.pts, a.gout, a.idx, a.bin_start, a.item_start, g,
+                                                    make_vol<float>(nullptr, L), dpad);
+    return cudaPeekAtLastError();
+}
+
 [[maybe_unused]] cudaError_t launch_adjoint_box(const ibr::BoxArgs &a, const ibl::Layout &L, float *dpad, cudaStream_t st)
 {
     if constexpr (SP::S == 3 && SP::K < 4 && SP::D <= 2) {
-        constexpr size_t smem = (size_t)ib::box_floats<SP>() * sizeof(float);
-        static_assert(smem <= kMaxSmem, "adjoint box must fit shared memory");
-        auto kern = ib::k_adjoint_box<SP>;
-        static unsigned long long configured = 0;          // per device: the attribute is set once
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e != cudaSuccess) return e;
-        if (dev >= 64 || !(configured >> dev & 1ull)) {
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            if (dev < 64) configured |= 1ull << dev;
-        }
-        ib::BoxGrid g;
-        g.nbins = a.nbins;
-        g.nb[0] = a.nb[0];
-        g.nb[1] = a.nb[1];
-        g.nb[2] = a.nb[2];
-        g.chunk = a.chunk;
-        kern<<<(unsigned)a.max_items, 256, smem, st>>>(static_cast<const float4 *>(a.q4), a.bin_start, a.item_start, g,
-                                                        make_vol<float>(nullptr, L), dpad);
-        return cudaPeekAtLastError();
+        constexpr int LB = ib::box_lb<SP>();
+        if (a.lb != LB) return cudaErrorInvalidValue;
+        return launch_adjoint_box_cfg<LB, ib::box_min_blocks<SP>()>(a, L, dpad, st);
     } else {
         return cudaErrorInvalidValue;
     }

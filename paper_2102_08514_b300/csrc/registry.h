@@ -26,13 +26,16 @@ using RayFn = cudaError_t (*)(const ibl::RayGeom &, const void *, const ibl::Lay
 using SortFn = cudaError_t (*)(const float *, int64_t, const ibl::Layout &, int, int, unsigned *, int, int32_t *,
                                float *, cudaStream_t);
 using DbgFn = cudaError_t (*)(const float *, int64_t, const ibl::Layout &, int32_t *, int32_t *, cudaStream_t);
-// the adjoint on spatially binned queries (x, y, z, gout) per query: (queries, bin starts, work
-// item starts, bins per axis and chunk, padded FP32 layout, gradient buffer, max work items)
+// the adjoint on spatially binned queries: the caller's points and gout, the query indices in
+// bin order, bin starts, work item starts, bins per axis and chunk, work items at most
 struct BoxArgs {
-    const void *q4;
+    const float *pts;
+    const float *gout;
+    const int *idx;
     const int *bin_start;
     const int *item_start;
     int nbins, nb[3], chunk, max_items;
+    int lb;          // log2 cells per bin and axis (SplineOps::box_lb)
 };
 using BoxAdjFn = cudaError_t (*)(const BoxArgs &, const ibl::Layout &, float *, cudaStream_t);
 
