@@ -597,7 +597,7 @@ def run_ours(args):
                          "peak_note": "random 4-byte gathers from a 16 MiB L2-resident buffer, measured in this run",
                          "ncu_l1_to_l2_request_cycles_frac": l1l2_frac}},
         "peaks": {k: pk[k] for k in ("sms", "fp32_tflops", "gather_gsectors_s", "gather4B_l1_gloads_s",
-                                     "red_gatomics_s", "l2_read_gbs", "clocks")},
+                                     "red_gatomics_s", "shared_atomic_f32_gops_s", "l2_read_gbs", "clocks")},
         "forms": {k: {"evals_per_s": (RAY_EVALS[0] if k.startswith("rays") else n) / (v * 1e-3), "ms": v}
                   for k, v in form_ms.items()},
     }
@@ -622,6 +622,9 @@ def run_ours(args):
     line["forms"]["adjoint"]["contributions_per_s"] = contrib / (form_ms["adjoint"] * 1e-3)
     line["forms"]["adjoint"]["over_l2_atomic_peak"] = contrib / (form_ms["adjoint"] * 1e-3) / (pk["red_gatomics_s"] * 1e9)
     line["forms"]["adjoint"]["over_value"] = form_ms["adjoint"] / form_ms["value"]
+    # the binned adjoint sums the contributions with shared-memory float atomics: their measured rate
+    line["forms"]["adjoint"]["over_shared_atomic_peak"] = (contrib / (form_ms["adjoint"] * 1e-3)
+                                                           / (pk["shared_atomic_f32_gops_s"] * 1e9))
     if args.workload != WORKLOAD or args.storage != "f32" or form != DEFAULT_FORM[WORKLOAD] or args.spline:
         line["metric"] = f"evals/s ({form}, {args.storage} storage)"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -216,11 +216,12 @@ interp_status interp_eval_host(interp_t *h, const float *pts, int64_t npts, floa
  * first for a plain gradient.  The scatter uses FP32 atomics into a handle-owned padded buffer,
  * so the order of additions, and the last bits of dcoeffs, vary between runs.  dcoeffs may be
  * NULL to compute dpts only.
- *   - 3-D splines with fewer than 4 pieces, calls with many queries (the contributions outnumber
- *     the shared-memory boxes' sites about twice; option "adjoint_bins" = 0 / 1 forces it off /
- *     on): the queries are first counting-sorted on the device into spatial bins of 16^3 (8^3 for
- *     FCC) coset cells; each bin's contributions are summed in a shared-memory box and added to
- *     the padded buffer once per site.  The scratch (16 bytes per query plus 16 per bin) comes
+ *   - 3-D splines with fewer than 4 pieces and at least 24 coefficient lookups per query, calls
+ *     with many queries (the contributions outnumber the shared-memory boxes' sites at least four
+ *     times; option "adjoint_bins" = 0 / 1 forces it off / on): the query indices are first
+ *     counting-sorted on the device into spatial bins of 8^3 coset cells; each bin's contributions
+ *     are summed in a shared-memory box and added to
+ *     the padded buffer once per site.  The scratch (8 bytes per query plus 16 per bin) comes
  *     from the library's stream-ordered pool (see the piece pre-sort); under stream capture, or
  *     when the pool has no room, the call takes the path below.
  *   - Otherwise, 3-D splines: each block of 1024 consecutive queries whose cells fit a small box

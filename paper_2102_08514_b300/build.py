@@ -97,7 +97,8 @@ def _unit_digest(cmd, kind) -> str:
     for name in UNIT_DEPS[kind]:
         with open(os.path.join(CSRC, name), "rb") as f:
             h.update(f.read())
-    for path in (GEN_HDR, os.path.join(ROOT, "include", "interp.h")):
+    # the C header only reaches the ABI unit; every unit includes the generated tables
+    for path in [GEN_HDR] + ([os.path.join(ROOT, "include", "interp.h")] if kind == "interp" else []):
         with open(path, "rb") as f:
             h.update(f.read())
     return h.hexdigest()

@@ -9,7 +9,9 @@
 //     request: the access pattern of the coefficient gathers of random queries) and from an
 //     L1-resident one (every load a hit: the L1 lookup rate of divergent loads);
 //   * L2 atomic throughput: red.global.add.f32 at pseudo-random addresses of an L2-resident
-//     buffer (the scatter of the adjoint).
+//     buffer (the scatter of the adjoint);
+//   * shared-memory atomic throughput, float and integer add at pseudo-random words (the
+//     binned adjoint sums its contributions with shared-memory float atomics).
 // Each entry point launches one kernel on the caller's stream; the caller times it with CUDA
 // events and converts with the work counts documented beside each entry point.
 #include <cuda_runtime.h>
@@ -120,6 +122,31 @@ __global__ void __launch_bounds__(128) k_red(float *__restrict__ buf, uint32_t m
     }
 }
 
+// shared-memory atomics: 8 per thread and round at pseudo-random words of a 16 KiB block-local
+// array, float add (T = 0) or 32-bit integer add (T = 1)
+template <int T>
+__global__ void __launch_bounds__(256) k_shared_atomic(int iters, float *__restrict__ out)
+{
+    __shared__ float sf[4096];
+    __shared__ unsigned su[4096];
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x) {
+        sf[i] = 0.0f;
+        su[i] = 0u;
+    }
+    __syncthreads();
+    uint32_t st = lcg(blockIdx.x * blockDim.x + threadIdx.x);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            st = lcg(st);
+            if constexpr (T == 0) atomicAdd(&sf[(st >> 8) & 4095u], 1.0f);
+            else atomicAdd(&su[(st >> 8) & 4095u], 1u);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) out[blockIdx.x] = sf[threadIdx.x] + (float)su[threadIdx.x];
+}
+
 }  // namespace
 
 extern "C" {
@@ -157,6 +184,17 @@ int peaks_gather(const float *buf, uint32_t mask, int width, int grid, int iters
 int peaks_red(float *buf, uint32_t mask, int grid, int iters, void *stream)
 {
     k_red<<<grid, 128, 0, static_cast<cudaStream_t>(stream)>>>(buf, mask, iters);
+    return (int)cudaPeekAtLastError();
+}
+
+// shared-memory atomics: count = grid * 256 * 8 * iters; type 0 float add, 1 integer add.  `out`
+// (grid floats) receives one value per CTA.
+int peaks_shared_atomic(int type, int grid, int iters, float *out, void *stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (type == 0) k_shared_atomic<0><<<grid, 256, 0, st>>>(iters, out);
+    else if (type == 1) k_shared_atomic<1><<<grid, 256, 0, st>>>(iters, out);
+    else return (int)cudaErrorInvalidValue;
     return (int)cudaPeekAtLastError();
 }
 

@@ -13,7 +13,9 @@
   coefficient gathers of random queries; ``gather{4,16,32}B_{l2,l1}_gloads_s`` the same for
   4-, 16- and 32-byte loads from L2- and L1-resident buffers (L1 lookups of divergent loads);
 * ``red_gatomics_s`` -- red.global.add.f32 at pseudo-random addresses of an L2-resident buffer
-  (the adjoint's scatter).
+  (the adjoint's scatter);
+* ``shared_atomic_{f32,u32}_gops_s`` -- shared-memory atomic adds at pseudo-random words, float
+  and integer (the binned adjoint's per-bin sums).
 
 The SM count comes from the device; the caller samples the SM clock around the calls (the
 per-clock figures divide by it).
@@ -41,7 +43,8 @@ def _lib():
         _LIB.peaks_l2_read.argtypes = [v, ctypes.c_int64, ctypes.c_int, ctypes.c_int, v, v]
         _LIB.peaks_gather.argtypes = [v, ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int, v, v]
         _LIB.peaks_red.argtypes = [v, ctypes.c_uint32, ctypes.c_int, ctypes.c_int, v]
-        for f in (_LIB.peaks_fma, _LIB.peaks_l2_read, _LIB.peaks_gather, _LIB.peaks_red):
+        _LIB.peaks_shared_atomic.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, v, v]
+        for f in (_LIB.peaks_fma, _LIB.peaks_l2_read, _LIB.peaks_gather, _LIB.peaks_red, _LIB.peaks_shared_atomic):
             f.restype = ctypes.c_int
     return _LIB
 
@@ -69,7 +72,7 @@ def _check(rc: int, what: str):
 
 
 def measure(torch=None) -> dict:
-    """Run the four microbenchmarks on the current device; rates as documented above."""
+    """Run the microbenchmarks on the current device; rates as documented above."""
     if torch is None:
         import torch
     lib = _lib()
@@ -119,6 +122,14 @@ def measure(torch=None) -> dict:
     ms = _best_ms(torch, lambda: _check(lib.peaks_red(ctypes.c_void_p(rbuf.data_ptr()), words - 1, ggrid, riters, st),
                                         "peaks_red"))
     res["red_gatomics_s"] = ggrid * 128 * 4 * riters / (ms * 1e-3) / 1e9
+
+    # shared-memory atomics, float and integer add: 8 CTAs of 256 threads per SM
+    sgrid, siters = sms * 8, 64
+    sout = torch.empty(sgrid, device="cuda")
+    for t, name in ((0, "shared_atomic_f32_gops_s"), (1, "shared_atomic_u32_gops_s")):
+        ms = _best_ms(torch, lambda: _check(lib.peaks_shared_atomic(t, sgrid, siters, ctypes.c_void_p(sout.data_ptr()), st),
+                                            "peaks_shared_atomic"))
+        res[name] = sgrid * 256 * 8 * siters / (ms * 1e-3) / 1e9
     torch.cuda.synchronize()
     return res
 
@@ -132,7 +143,9 @@ def per_clock(res: dict, sm_mhz: float) -> dict:
             "gather_sectors_per_clk_per_sm": res["gather_gsectors_s"] * 1e9 / (sms * hz),
             **{k.replace("_gloads_s", "_loads_per_clk_per_sm"): v * 1e9 / (sms * hz)
                for k, v in res.items() if k.endswith("_gloads_s")},
-            "red_per_clk_per_sm": res["red_gatomics_s"] * 1e9 / (sms * hz)}
+            "red_per_clk_per_sm": res["red_gatomics_s"] * 1e9 / (sms * hz),
+            "shared_atomic_f32_per_clk_per_sm": res["shared_atomic_f32_gops_s"] * 1e9 / (sms * hz),
+            "shared_atomic_u32_per_clk_per_sm": res["shared_atomic_u32_gops_s"] * 1e9 / (sms * hz)}
 
 
 if __name__ == "__main__":
