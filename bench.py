@@ -61,13 +61,37 @@ def presort_applies(info, n: int) -> bool:
     return bool(info.presort) and n >= (1 << 16)
 
 
-def launches_per_step(form: str, n: int, presort: bool) -> int:
+def adjoint_bins_apply(info, n: int) -> bool:
+    """Whether interp_backward on n queries takes the binned adjoint with the handle's default
+    options (the library's rule: 3-D spline with < 4 pieces and >= 24 lookups per query, and the
+    contributions at least four times the sites of the bins' shared-memory boxes; bins of 8^3
+    coset cells over the padded arrays, boxes of 8 + 2 halo + 2 sites per axis and coset), or
+    INTERP_B300_ADJOINT_BINS=0 / 1."""
+    if info.s != 3 or info.n_pieces >= 4 or info.D > 2:
+        return False
+    env = os.environ.get("INTERP_B300_ADJOINT_BINS")
+    if env:
+        return env[0] == "1"
+    if info.lookups_per_query < 24:
+        return False
+    nbins = 1
+    for a in range(3):
+        pdims = -(-(info.dims[a] + 4 * info.halo) // 2) * 2
+        nbins *= -(-pdims // 8)
+    w = 8 + 2 * info.halo + 2
+    return n * info.lookups_per_query >= 4.0 * nbins * info.n_cosets * w ** 3
+
+
+def launches_per_step(form: str, n: int, presort: bool, adjoint_bins: bool = False) -> int:
     """This library's kernels in one step: the evaluation kernel (value forms), or the adjoint
-    kernel and the unpadding add (adjoint); with the pre-sort, per chunk of 2^22 queries the piece
-    classifier, count, scan and scatter kernels before the evaluation (adjoint) kernel, and the
-    un-permute after it (value forms)."""
+    kernel and the unpadding add (adjoint); the binned adjoint adds its count, scan and scatter
+    kernels; with the pre-sort, per chunk of 2^22 queries the piece classifier, count, scan and
+    scatter kernels before the evaluation (adjoint) kernel, and the un-permute after it (value
+    forms)."""
     chunks = -(-n // (1 << 22))
     if form == "adjoint":
+        if adjoint_bins:
+            return 5
         return (5 * chunks if presort else 1) + 1
     return 6 * chunks if presort else 1
 
@@ -576,7 +600,7 @@ def run_ours(args):
                                "both_directions_at_once_ms": both_ms, "frac_of_both": both_ms / e2e_ms,
                                "note": "plain pinned copies of the step's bytes: the larger of the two directions "
                                        "alone, and both directions at once on two streams"}},
-        "gpu_launches": args.steps * launches_per_step(form, n, presort),
+        "gpu_launches": args.steps * launches_per_step(form, n, presort, adjoint_bins_apply(info, n)),
         "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": kname,
@@ -595,7 +619,12 @@ def run_ours(args):
                          "peak_gsectors_s": pk["gather_gsectors_s"],
                          "frac": sectors * n / (kern_ms * 1e-3) / 1e9 / pk["gather_gsectors_s"] if sectors else None,
                          "peak_note": "random 4-byte gathers from a 16 MiB L2-resident buffer, measured in this run",
-                         "ncu_l1_to_l2_request_cycles_frac": l1l2_frac}},
+                         "ncu_l1_to_l2_request_cycles_frac": l1l2_frac,
+                         # every coefficient is one L1 lookup (hit or miss): against the measured
+                         # rate of random L1-hit gathers
+                         "l1_lookups_per_query": info.lookups_per_query,
+                         "l1_lookup_frac": info.lookups_per_query * n / (kern_ms * 1e-3) / (pk["gather4B_l1_gloads_s"] * 1e9)
+                         if form != "adjoint" else None}},
         "peaks": {k: pk[k] for k in ("sms", "fp32_tflops", "gather_gsectors_s", "gather4B_l1_gloads_s",
                                      "red_gatomics_s", "shared_atomic_f32_gops_s", "l2_read_gbs", "clocks")},
         "forms": {k: {"evals_per_s": (RAY_EVALS[0] if k.startswith("rays") else n) / (v * 1e-3), "ms": v}

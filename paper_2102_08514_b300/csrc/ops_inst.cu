@@ -2,6 +2,7 @@
 // compiles this file once per (spline, family) with -DINTERP_SPLINE=<name> -DINTERP_PART=<0..3>
 // so the large unrolled kernels compile in parallel.
 #include <algorithm>
+#include <atomic>
 
 #include "kernels.cuh"
 #include "registry.h"
@@ -35,6 +36,17 @@ inline unsigned grid_for(int64_t n) { return (unsigned)((n + kTPB - 1) / kTPB); 
 // shared memory a CTA may use (opt-in maximum on sm_100 / sm_103)
 constexpr size_t kMaxSmem = 227 * 1024;
 
+// a kernel attribute is set once per device: one bit per device (devices >= 64 set it every call);
+// several host threads may launch at once
+inline bool attr_pending(const std::atomic<unsigned long long> &done, int dev)
+{
+    return dev >= 64 || !((done.load(std::memory_order_acquire) >> dev) & 1ull);
+}
+inline void attr_set(std::atomic<unsigned long long> &done, int dev)
+{
+    if (dev < 64) done.fetch_or(1ull << dev, std::memory_order_release);
+}
+
 // piece-binned kernel configurations: (tile of queries, threads per CTA)
 template <class CT, int MODE, int T, int NT, bool DENSE = false>
 [[maybe_unused]] cudaError_t launch_binned_cfg(const float *pts, int64_t n, const void *c, const ibl::Layout &L,
@@ -43,14 +55,14 @@ template <class CT, int MODE, int T, int NT, bool DENSE = false>
     constexpr size_t smem = ib::binned_smem_bytes<SP, MODE, T>();
     static_assert(smem <= kMaxSmem, "binned tile must fit shared memory");
     auto kern = ib::k_eval_binned<SP, CT, MODE, T, NT, DENSE>;
-    static unsigned long long configured = 0;          // per device: the attribute is set once
+    static std::atomic<unsigned long long> configured{0};   // per device: the attribute is set once
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev >= 64 || !(configured >> dev & 1ull)) {
+    if (attr_pending(configured, dev)) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        if (dev < 64) configured |= 1ull << dev;
+        attr_set(configured, dev);
     }
     const unsigned grid = (unsigned)((n + T - 1) / T);
     kern<<<grid, NT, smem, st>>>(pts, n, make_vol<CT>(c, L), out, grad, gout);
@@ -121,14 +133,14 @@ cudaError_t launch_eval(const float *pts, int64_t n, const void *c, const ibl::L
         constexpr size_t smem = ib::binned_adjoint_smem_bytes<SP, T>();
         static_assert(smem <= kMaxSmem, "binned adjoint tile must fit shared memory");
         auto kern = ib::k_adjoint_binned<SP, T, NT>;
-        static unsigned long long configured = 0;
+        static std::atomic<unsigned long long> configured{0};
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
-        if (dev >= 64 || !(configured >> dev & 1ull)) {
+        if (attr_pending(configured, dev)) {
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            if (dev < 64) configured |= 1ull << dev;
+            attr_set(configured, dev);
         }
         kern<<<(unsigned)((n + T - 1) / T), NT, smem, st>>>(pts, n, gout, make_vol<float>(nullptr, L), dpad);
     } else {
@@ -145,14 +157,14 @@ template <int LB, int MINB>
     constexpr size_t smem = (size_t)ib::box_floats<SP, LB>() * sizeof(float);
     static_assert(smem <= kMaxSmem, "adjoint box must fit shared memory");
     auto kern = ib::k_adjoint_box<SP, LB, MINB>;
-    static unsigned long long configured = 0;          // per device: the attribute is set once
+    static std::atomic<unsigned long long> configured{0};   // per device: the attribute is set once
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev >= 64 || !(configured >> dev & 1ull)) {
+    if (attr_pending(configured, dev)) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        if (dev < 64) configured |= 1ull << dev;
+        attr_set(configured, dev);
     }
     ib::BoxGrid g;
     g.nbins = a.nbins;
@@ -223,16 +235,16 @@ template <bool GRAD>
                 auto kd = ib::k_rays_binned<SP, GRAD, T, 512, SP::DENSE>;
                 auto kp = ib::k_rays_binned<SP, GRAD, T, 512>;
                 auto kern = dense ? kd : kp;
-                static unsigned long long configured = 0;       // both variants, once per device
+                static std::atomic<unsigned long long> configured{0};   // both variants, once per device
                 int dev = 0;
                 cudaError_t e = cudaGetDevice(&dev);
                 if (e != cudaSuccess) return e;
-                if (dev >= 64 || !(configured >> dev & 1ull)) {
+                if (attr_pending(configured, dev)) {
                     e = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                     if (e == cudaSuccess && SP::DENSE)
                         e = cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                     if (e != cudaSuccess) return e;
-                    if (dev < 64) configured |= 1ull << dev;
+                    attr_set(configured, dev);
                 }
                 const int64_t rays = (int64_t)rg.width * rg.height;
                 const int rt = T / rg.steps;
