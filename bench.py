@@ -54,10 +54,10 @@ def peaks():
 def presort_applies(info, n: int) -> bool:
     """Whether an evaluation call of n queries takes the library's piece pre-sort: its default for
     this spline (interp_info_t.presort) at >= 2^16 queries, or INTERP_B300_PRESORT=0 / 1 (any
-    multi-piece spline)."""
+    spline whose evaluation runs the piece-binned kernels, interp_info_t.binned)."""
     env = os.environ.get("INTERP_B300_PRESORT")
     if env:
-        return env[0] == "1" and info.n_pieces >= 4
+        return env[0] == "1" and bool(info.binned)
     return bool(info.presort) and n >= (1 << 16)
 
 
@@ -126,16 +126,21 @@ def brick_lb(s, esz, M, a):
 def distinct_sectors_per_query(spline: str, pts, esz: int = 4):
     """Mean number of distinct 32-byte sectors (bricks) a query's coefficient gathers touch: the
     gather work of one query in the library's bricked layout, which bounds random queries (each
-    distinct sector is one L1 miss and one L1 -> L2 request).  One-piece 3-D splines only (the
-    stencil is then the same for every folded point); None otherwise.  Follows the kernels'
-    steps: nearest coset site, |y| sorted descending (signed permutation), the piece's stencil."""
+    distinct sector is one L1 miss and one L1 -> L2 request).  3-D box splines (one stencil per
+    piece); None otherwise.  Follows the kernels' steps: nearest coset site, |y| sorted descending
+    (signed permutation), the piece from the plane bits through sigma, the piece's stencil."""
     import json as _json
+    from fractions import Fraction
     with open(os.path.join(ROOT, "paper_2102_08514_b300", "csrc", "generated", "splines.json")) as f:
         meta = _json.load(f)["splines"][spline]
-    if meta["s"] != 3 or len(meta["pieces"]) != 1:
+    if meta["s"] != 3 or meta["kind"] != 0:
         return None
     D, H, cosets = meta["D"], meta["halo"], np.asarray(meta["cosets"])
-    site = np.asarray(meta["pieces"][0]["sites"])
+    ns = max(len(pc["sites"]) for pc in meta["pieces"])
+    # every piece's stencil padded to the longest with its first site (no new sector)
+    sites = np.asarray([pc["sites"] + [pc["sites"][0]] * (ns - len(pc["sites"])) for pc in meta["pieces"]])
+    planes = [(np.asarray(pv, dtype=np.float64), float(Fraction(e))) for pv, e in meta["planes"]]
+    sigma = np.asarray(meta["sigma"])
     M = len(cosets)
     lbs = [brick_lb(3, esz, M, a) for a in range(3)]
     x = np.asarray(pts, dtype=np.float64)
@@ -147,11 +152,16 @@ def distinct_sectors_per_query(spline: str, pts, esz: int = 4):
         y = u - D * i
         sg = np.where(y < 0, -1, 1)
         order = np.argsort(-np.abs(y), axis=1, kind="stable")
-        P = np.repeat((i + 2 * H)[:, None, :], len(site), axis=1)
+        t = -np.sort(-np.abs(y), axis=1)
+        q = np.zeros(n, dtype=np.int64)
+        for b, (pv, e) in enumerate(planes):
+            q |= ((t @ pv - e) >= 0).astype(np.int64) << b
+        site = sites[sigma[q]]                                 # n x ns x 3
+        P = np.repeat((i + 2 * H)[:, None, :], ns, axis=1)
         rows = np.arange(n)
         for A in range(3):
             ax = order[:, A]
-            P[rows, :, ax] += (sg[rows, ax][:, None] * site[None, :, A])
+            P[rows, :, ax] += (sg[rows, ax][:, None] * site[:, :, A])
         b = np.zeros(P.shape[:2], dtype=np.int64)
         for a in range(3):
             b = b * 4096 + (P[..., a] >> lbs[a])

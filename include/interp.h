@@ -33,7 +33,8 @@
  *     a chunk) comes per call from a stream-ordered memory pool owned by the library (cached up
  *     to 1 GiB per device); under stream capture, or when the pool has no room, the call runs
  *     without the sort.  interp_backward_noalloc never sorts.  The handle's "presort" option
- *     (interp_set_option) forces the sort off / on for any multi-piece spline and call size.
+ *     (interp_set_option) forces the sort off / on for any call size: evaluation calls that run
+ *     the piece-binned kernels, interp_backward calls of splines with >= 4 pieces.
  *   - Launch options are per handle (interp_set_option).  Their initial values are read from the
  *     environment once, when the handle is created: INTERP_B300_BINNED, INTERP_B300_PRESORT,
  *     INTERP_B300_DENSE, INTERP_B300_ADJOINT_BINS (0 / 1) and INTERP_B300_BINCFG (=small); later changes of the
@@ -130,16 +131,20 @@ typedef struct {
     int kind;                     /* 0: box spline; n >= 1: Voronoi spline V_n              */
     int presort;                  /* 1: calls of >= 2^16 queries take the piece pre-sort by  */
                                   /*    default (see the conventions above)                 */
+    int binned;                   /* 1: evaluation runs the piece-binned kernels by default  */
+                                  /*    (>= 4 pieces with >= 200 nonzeros of A_j in all)     */
 } interp_info_t;
 interp_status interp_info(const interp_t *h, interp_info_t *info);
 
 /*
  * interp_set_option / interp_get_option -- per-handle launch options (not in the paper; they
  * select among equivalent kernels, results are the same bits except where noted):
- *   "binned"           -1 default (piece-binned kernels for splines with >= 4 pieces), 0 plain
+ *   "binned"           -1 default (piece-binned kernels where interp_info_t.binned is 1: >= 4
+ *                      pieces with >= 200 nonzeros of A_j in all; the rays of value + gradient
+ *                      of splines whose pieces have <= 100 nonzeros each stay plain), 0 plain
  *                      kernels, 1 piece-binned kernels for any multi-piece spline
- *   "presort"          -1 default (see the piece pre-sort above), 0 never, 1 every call of a
- *                      multi-piece spline (adjoint sums change order, see interp_backward)
+ *   "presort"          -1 default (see the piece pre-sort above), 0 never, 1 every call that
+ *                      can take it (adjoint sums change order, see interp_backward)
  *   "dense"            -1 default (dense piece tables for the rays of the splines that have
  *                      them), 0 never, 1 also for the binned evaluation
  *   "bin_small_tiles"  0 default, 1 binned kernels on 256-query tiles of 128-thread CTAs

@@ -599,10 +599,12 @@ static cudaError_t eval_launch(const interp *h, const float *pts, int64_t npts, 
                                int mode, cudaStream_t st, bool allow_presort = true)
 {
     const int dt = h->storage == INTERP_F32 ? 0 : (h->storage == INTERP_F16 ? 1 : 2);
-    // splines with many pieces (D4*: 6) run the piece-binned kernel; with few small pieces (FCC: 3)
-    // the sort costs more than the divergence it removes (measured).  The handle's "binned"
-    // option forces the plain / binned kernel.
-    const bool want = h->opt_binned >= 0 ? h->opt_binned == 1 : h->ops->K >= 4;
+    // splines whose pieces' divergent work is large (>= 4 pieces, >= 200 nonzeros of A_j in all:
+    // D4*, BCC V_1 and V_2, FCC V_2) run the piece-binned kernel; for few or small pieces (FCC:
+    // 3 pieces, FCC V_1: 74 nonzeros) the sort costs more than the divergence it removes
+    // (measured; ops_inst.cu's binned_default).  The handle's "binned" option forces the plain /
+    // binned kernel.
+    const bool want = h->opt_binned >= 0 ? h->opt_binned == 1 : h->ops->binned_eval;
     const bool binned = want && h->ops->eval_binned[dt][mode];
     const ibr::EvalFn fn = (binned ? h->ops->eval_binned : h->ops->eval)[dt][mode];
     const int flags = launch_flags(h);
@@ -1167,6 +1169,7 @@ interp_status interp_info(const interp_t *h, interp_info_t *info)
     info->name = o.name;
     info->kind = o.kind;
     info->presort = presort_default(&o) ? 1 : 0;
+    info->binned = o.binned_eval ? 1 : 0;
     return INTERP_OK;
 }
 

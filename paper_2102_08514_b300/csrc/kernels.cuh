@@ -646,6 +646,74 @@ __device__ __forceinline__ void eval_piece_dense(const Fold<SP::S> &f, const Dev
     }
 }
 
+// true when stencil slot M lies at the same offset in every piece that has it (then no per-piece
+// select is needed for its address)
+template <class SP, int M>
+constexpr bool slot_shared()
+{
+    bool same = M < SP::NS[0];
+    for (int j = 1; j < SP::K && same; ++j)
+        for (int a = 0; a < SP::S && M < SP::NS[j]; ++a) same = same && SP::SITE[j][M][a] == SP::SITE[0][M][a];
+    return same;
+}
+
+// steps 4-5 for the run-time piece j of a query whose warp may hold several pieces.  The pieces
+// share one monomial space, so only b = A_j c differs in code between them: the site offsets and
+// anchors are selected per piece, the coefficient loads, the Horner evaluation and the unfold of
+// the gradient run once for every lane, and only the accumulation of b branches.  b accumulates
+// each piece's nonzeros in the same order as eval_piece, so both give the same sums.
+template <class SP, bool GRAD, class CT>
+__device__ __forceinline__ void eval_piece_shared(const Fold<SP::S> &f, const DevVol<CT> &v, float &val,
+                                                  float (&grad)[SP::S])
+{
+    constexpr int S = SP::S;
+    constexpr int NM = SP::NMON;
+    constexpr int NSM = SP::NSMAX;
+    const int j = f.piece;
+    const CT *cb = v.c + f.base;
+    float c[NSM];
+    sfor<NSM>([&](auto Mi) {
+        constexpr int m = decltype(Mi)::value;
+        // a slot that piece j lacks reads the cell's own site (in range, usually a hit); its value
+        // is not used
+        int off = 0;
+        if constexpr (slot_shared<SP, m>()) {
+            off = site_offset<SP, 0, m>(f);
+        } else {
+            sfor<SP::K>([&](auto Jc) {
+                constexpr int J = decltype(Jc)::value;
+                if constexpr (m < SP::NS[J]) {
+                    if (j == J) off = site_offset<SP, J, m>(f);
+                }
+            });
+        }
+        c[m] = load_coef<CT>(cb + off);
+    });
+    float t[S];
+    sfor<S>([&](auto A) {
+        constexpr float an0 = SP::ANCHOR[0][decltype(A)::value];
+        float an = an0;
+        sfor<SP::K - 1>([&](auto Jc) {
+            constexpr float anj = SP::ANCHOR[decltype(Jc)::value + 1][decltype(A)::value];
+            if (j == decltype(Jc)::value + 1) an = anj;
+        });
+        t[A] = f.t[A] - an;
+    });
+    float b[NM];
+    sfor<NM>([&](auto A) { b[A] = 0.0f; });
+    sfor<SP::K>([&](auto Jc) {
+        constexpr int J = decltype(Jc)::value;
+        if (j == J) accumulate<NSM, NM>(b, c, typename SP::template NZL<J>{});
+    });
+    if constexpr (!GRAD) {
+        val += horner<S, S, SP::DEG, 0, NM>(b, t);
+    } else {
+        const VG<S> r = horner_grad<S, S, SP::DEG, 0, NM>(b, t);
+        val += r.v;
+        unfold_grad<S>(f, r.g, grad);
+    }
+}
+
 // one binned item of piece j: the dense path or the piece's unrolled code
 template <class SP, bool GRAD, class CT, bool DENSE>
 __device__ __forceinline__ void eval_item(const Fold<SP::S> &f, const DevVol<CT> &v, int j, float &val,
@@ -671,14 +739,22 @@ __device__ __forceinline__ void eval_point(const float (&x)[SP::S], const DevVol
             if (f.in_range) eval_piece<SP, 0, GRAD, CT>(f, v, val, grad);
         });
     } else {
-        // several pieces: one copy of each piece's code, run-time coset loop
+        // several pieces: run-time coset loop; the pieces share all code but the accumulation of
+        // b (monomial spaces up to 120; up to six pieces, or more with small A_j), else one copy of
+        // each piece's code (many large pieces: the per-piece address selects would cost more
+        // than the shared code saves)
 #pragma unroll 1
         for (int k = 0; k < SP::M; ++k) {
             const auto f = fold_coset<SP, -1, CT>(x, v, k);
             if (f.in_range) {
-                sfor<SP::K>([&](auto Jc) {
-                    if (f.piece == decltype(Jc)::value) eval_piece<SP, decltype(Jc)::value, GRAD, CT>(f, v, val, grad);
-                });
+                if constexpr (SP::NMON <= 120 && (SP::K <= 6 || SP::NNZMAX <= 100)) {
+                    eval_piece_shared<SP, GRAD, CT>(f, v, val, grad);
+                } else {
+                    sfor<SP::K>([&](auto Jc) {
+                        if (f.piece == decltype(Jc)::value)
+                            eval_piece<SP, decltype(Jc)::value, GRAD, CT>(f, v, val, grad);
+                    });
+                }
             }
         }
     }

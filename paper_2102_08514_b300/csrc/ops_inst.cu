@@ -36,6 +36,28 @@ inline unsigned grid_for(int64_t n) { return (unsigned)((n + kTPB - 1) / kTPB); 
 // shared memory a CTA may use (opt-in maximum on sm_100 / sm_103)
 constexpr size_t kMaxSmem = 227 * 1024;
 
+constexpr int nnz_sum()
+{
+    int t = 0;
+    for (int j = 0; j < SP::K; ++j) t += SP::NNZ[j];
+    return t;
+}
+
+// whether the piece-binned kernels are the default for evaluation (GRAD: value + gradient).
+// Sorting a tile's items by piece pays when the pieces' divergent work is large: the plain kernel
+// shares all but the accumulation of b between the pieces, so a warp pays the sum of the pieces'
+// nonzeros once per coset.  Measured, 2^24 / 2^22 random queries, plain against binned: FCC V_1
+// (4 pieces, 74 nonzeros in all) value 0.175 / 0.323 ms, value + grad 0.208 / 0.358 ms; BCC V_1
+// (14 pieces, 848) 0.900 / 0.649, 0.960 / 0.787; FCC V_2 (4, 1361) 0.774 / 0.554; D4* (6, 5530)
+// 6.76 / 2.82 ms.  Rays (RAYS) of value + gradient with small pieces stay plain (BCC V_1,
+// 1024^2 x 256: value 11.66 / 11.23 ms, value + grad 12.32 / 15.69 ms).
+template <bool GRAD, bool RAYS>
+constexpr bool binned_default()
+{
+    if constexpr (SP::K < 4 || nnz_sum() < 200) return false;
+    else return !(RAYS && GRAD && SP::NNZMAX <= 100);
+}
+
 // a kernel attribute is set once per device: one bit per device (devices >= 64 set it every call);
 // several host threads may launch at once
 inline bool attr_pending(const std::atomic<unsigned long long> &done, int dev)
@@ -222,10 +244,12 @@ template <bool GRAD>
 {
     if constexpr (SP::S == 3) {
         if constexpr (SP::K > 1) {
-            // multi-piece splines: whole rays per tile, samples binned by piece (as eval_launch:
-            // default for K >= 4, FLAG_BINNED_OFF / FLAG_BINNED_ON force the plain / binned kernel)
+            // multi-piece splines: whole rays per tile, samples binned by piece (default as
+            // binned_default, FLAG_BINNED_OFF / FLAG_BINNED_ON force the plain / binned kernel)
             constexpr int T = bin_tile<GRAD ? 1 : 0>();
-            const bool want = (flags & ibr::FLAG_BINNED_ON) ? true : (flags & ibr::FLAG_BINNED_OFF) ? false : SP::K >= 4;
+            const bool want = (flags & ibr::FLAG_BINNED_ON)    ? true
+                              : (flags & ibr::FLAG_BINNED_OFF) ? false
+                                                               : binned_default<GRAD, true>();
             if (want && rg.steps >= 1 && rg.steps <= T) {
                 constexpr size_t smem = ib::binned_smem_bytes<SP, GRAD ? 1 : 0, T>();
                 static_assert(smem <= kMaxSmem, "binned tile must fit shared memory");
@@ -283,6 +307,8 @@ void IB_CAT(fill_, INTERP_SPLINE, _, INTERP_PART)(SplineOps &o)
     o.fma_value = SP::FMA_VALUE;
     o.fma_grad = SP::FMA_GRAD;
     o.lookups = SP::LOOKUPS;
+    o.nnz_sum = nnz_sum();
+    o.binned_eval = binned_default<false, false>();
     o.adjoint = launch_adjoint;
     if constexpr (SP::S == 3 && SP::K < 4 && SP::D <= 2) {
         o.adjoint_box = launch_adjoint_box;

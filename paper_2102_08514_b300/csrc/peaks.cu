@@ -106,6 +106,33 @@ __global__ void __launch_bounds__(128) k_gather(const float *__restrict__ buf, u
     if (acc == 1234.5f) out[t] = acc;
 }
 
+// groups of G lanes (adjacent lanes of one warp) share a pseudo-random 128-byte line: in every
+// load instruction lane r of a group reads the word at float offset r * (32 / G) of its group's
+// line, so one instruction asks for G different sectors of each of 32 / G lines (the buffer holds
+// mask + 1 lines of 32 floats; mask + 1 a power of two)
+template <int G>
+__global__ void __launch_bounds__(128) k_gather_lines(const float *__restrict__ buf, uint32_t mask, int iters,
+                                                      float *__restrict__ out)
+{
+    uint32_t st[8];
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t grp = t / G, r = t % G;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) st[u] = lcg(grp * 8u + (uint32_t)u + 0x9e3779b9u);
+    float acc = 0.0f;
+    for (int i = 0; i < iters; ++i) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            st[u] = lcg(st[u]);
+            v[u] = __ldg(buf + 32 * (size_t)((st[u] >> 4) & mask) + r * (32 / G));
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += v[u];
+    }
+    if (acc == 1234.5f) out[t] = acc;
+}
+
 // each thread: `iters` rounds of 4 red.global.add.f32 at pseudo-random word addresses
 __global__ void __launch_bounds__(128) k_red(float *__restrict__ buf, uint32_t mask, int iters)
 {
@@ -176,6 +203,18 @@ int peaks_gather(const float *buf, uint32_t mask, int width, int grid, int iters
     if (width == 1) k_gather<1><<<grid, 128, 0, st>>>(buf, mask, iters, out);
     else if (width == 4) k_gather<4><<<grid, 128, 0, st>>>(buf, mask, iters, out);
     else if (width == 8) k_gather<8><<<grid, 128, 0, st>>>(buf, mask, iters, out);
+    else return (int)cudaErrorInvalidValue;
+    return (int)cudaPeekAtLastError();
+}
+
+// random line gathers: grid * 128 * 8 * iters loads, groups of `group` (1, 2 or 4) lanes on one
+// line; buf holds mask + 1 lines of 128 bytes
+int peaks_gather_lines(const float *buf, uint32_t mask, int group, int grid, int iters, float *out, void *stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (group == 1) k_gather_lines<1><<<grid, 128, 0, st>>>(buf, mask, iters, out);
+    else if (group == 2) k_gather_lines<2><<<grid, 128, 0, st>>>(buf, mask, iters, out);
+    else if (group == 4) k_gather_lines<4><<<grid, 128, 0, st>>>(buf, mask, iters, out);
     else return (int)cudaErrorInvalidValue;
     return (int)cudaPeekAtLastError();
 }

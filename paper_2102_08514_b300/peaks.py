@@ -12,6 +12,9 @@
   buffer, one 32-byte sector (one L1 -> L2 miss request) each: the rate that bounds the
   coefficient gathers of random queries; ``gather{4,16,32}B_{l2,l1}_gloads_s`` the same for
   4-, 16- and 32-byte loads from L2- and L1-resident buffers (L1 lookups of divergent loads);
+* ``gather_line{1,2,4}_gsectors_s`` -- the same 4-byte gathers with groups of 1, 2 or 4 lanes
+  reading different sectors of one pseudo-random 128-byte line in every instruction: sectors per
+  second when one L1 -> L2 request carries 1, 2 or 4 sectors;
 * ``red_gatomics_s`` -- red.global.add.f32 at pseudo-random addresses of an L2-resident buffer
   (the adjoint's scatter);
 * ``shared_atomic_{f32,u32}_gops_s`` -- shared-memory atomic adds at pseudo-random words, float
@@ -42,9 +45,11 @@ def _lib():
         _LIB.peaks_fma.argtypes = [ctypes.c_int, ctypes.c_int, v, v]
         _LIB.peaks_l2_read.argtypes = [v, ctypes.c_int64, ctypes.c_int, ctypes.c_int, v, v]
         _LIB.peaks_gather.argtypes = [v, ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int, v, v]
+        _LIB.peaks_gather_lines.argtypes = [v, ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int, v, v]
         _LIB.peaks_red.argtypes = [v, ctypes.c_uint32, ctypes.c_int, ctypes.c_int, v]
         _LIB.peaks_shared_atomic.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, v, v]
-        for f in (_LIB.peaks_fma, _LIB.peaks_l2_read, _LIB.peaks_gather, _LIB.peaks_red, _LIB.peaks_shared_atomic):
+        for f in (_LIB.peaks_fma, _LIB.peaks_l2_read, _LIB.peaks_gather, _LIB.peaks_gather_lines, _LIB.peaks_red,
+                  _LIB.peaks_shared_atomic):
             f.restype = ctypes.c_int
     return _LIB
 
@@ -115,6 +120,13 @@ def measure(torch=None) -> dict:
             res[f"gather{width * 4}B_{where}_gloads_s"] = loads / (ms * 1e-3) / 1e9
     res["gather_gsectors_s"] = res["gather4B_l2_gloads_s"]
     res["gather_buffer_bytes"] = words * 4
+    # the same 16 MiB as lines of 128 bytes, 1, 2 or 4 lanes per line and instruction
+    for group in (1, 2, 4):
+        ms = _best_ms(torch, lambda: _check(lib.peaks_gather_lines(ctypes.c_void_p(gbuf.data_ptr()), words // 32 - 1,
+                                                                   group, ggrid, giters,
+                                                                   ctypes.c_void_p(gout.data_ptr()), st),
+                                            "peaks_gather_lines"))
+        res[f"gather_line{group}_gsectors_s"] = loads / (ms * 1e-3) / 1e9
 
     # random L2 atomics into 16 MiB
     rbuf = torch.zeros(words, device="cuda")

@@ -72,3 +72,12 @@ def test_option_argument_errors_without_gpu(lib):
     v = ctypes.c_int()
     assert h.interp_get_option(None, b"presort", ctypes.byref(v)) == binding.INTERP_EINVAL
     assert h.interp_debug_device_allocations() >= 0
+
+
+def test_peaks_library_exports_its_microbenchmarks():
+    import ctypes
+    from paper_2102_08514_b300 import peaks
+    plib = ctypes.CDLL(peaks.library_path())
+    for name in ("peaks_fma", "peaks_l2_read", "peaks_gather", "peaks_gather_lines", "peaks_red",
+                 "peaks_shared_atomic"):
+        assert hasattr(plib, name), name

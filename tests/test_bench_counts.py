@@ -42,12 +42,41 @@ def test_adjoint_bins_apply(monkeypatch):
 
 def test_presort_applies(monkeypatch):
     monkeypatch.delenv("INTERP_B300_PRESORT", raising=False)
-    on = types.SimpleNamespace(presort=1, n_pieces=14)
-    off = types.SimpleNamespace(presort=0, n_pieces=6)
+    on = types.SimpleNamespace(presort=1, n_pieces=14, binned=1)
+    off = types.SimpleNamespace(presort=0, n_pieces=6, binned=1)
     assert bench.presort_applies(on, 1 << 16) and not bench.presort_applies(on, (1 << 16) - 1)
     assert not bench.presort_applies(off, 1 << 24)
     monkeypatch.setenv("INTERP_B300_PRESORT", "1")
     assert bench.presort_applies(off, 10)
-    assert not bench.presort_applies(types.SimpleNamespace(presort=0, n_pieces=1), 1 << 24)
+    assert not bench.presort_applies(types.SimpleNamespace(presort=0, n_pieces=1, binned=0), 1 << 24)
+    assert not bench.presort_applies(types.SimpleNamespace(presort=0, n_pieces=4, binned=0), 1 << 24)
     monkeypatch.setenv("INTERP_B300_PRESORT", "0")
     assert not bench.presort_applies(on, 1 << 24)
+
+
+def test_distinct_sectors_match_the_support():
+    """The sector count walks the kernels' fold, piece and stencil; here the same count from the
+    oracle's support instead: every coset site n with phi(x - n) != 0, bricked the same way."""
+    import numpy as np
+    import oracle
+    from synth import LATTICES, SPLINES, WORKLOADS, interior_box, make_rng, uniform_points
+    for wname in ("bcc_quintic_128", "fcc_6dir_128"):
+        wl = WORKLOADS[wname]
+        sp = SPLINES[wl.spline]
+        lat = LATTICES[sp.lattice]
+        xi = np.asarray(sp.xi)
+        o = oracle.Spline(xi, abs(round(np.linalg.det(np.asarray(lat.L, dtype=float)))))
+        D, M, H = lat.D, len(lat.cosets), 2 if wl.spline == "bcc_quintic" else 1
+        lbs = [bench.brick_lb(3, 4, M, a) for a in range(3)]
+        lo, hi = interior_box(wl.spline, wl.dims)
+        pts = uniform_points(make_rng(7, 1), 24, lo, hi)
+        grid = np.stack(np.meshgrid(*[np.arange(-3, 4)] * 3, indexing="ij"), -1).reshape(-1, 3)
+        for x in pts.astype(np.float64):
+            keys = set()
+            for k, l in enumerate(lat.cosets):
+                i = np.floor((x - l) / D).astype(np.int64) + grid
+                val = o.phi(x - (D * i + np.asarray(l)))
+                for ii in i[val != 0]:
+                    P = ii + 2 * H
+                    keys.add((k,) + tuple(int(P[a]) >> lbs[a] for a in range(3)))
+            assert bench.distinct_sectors_per_query(wl.spline, x[None].astype(np.float32)) == len(keys), (wname, x)

@@ -259,14 +259,18 @@ def test_full_size_headline_workload_sampled():
     assert np.abs(grad.cpu().numpy()[idx] - ref_g).max() <= VALUE_TOL * cmax * G
 
 
-@pytest.mark.parametrize("name", ["fcc_6dir", "d4s_8dir", "d4_8dir", "bcc_voronoi1", "fcc_voronoi2", "bcc_voronoi2"])
+@pytest.mark.parametrize("name", ["fcc_6dir", "d4s_8dir", "d4_8dir", "bcc_voronoi1", "fcc_voronoi1", "fcc_voronoi2",
+                                  "bcc_voronoi2"])
 def test_piece_binned_kernel_equals_plain_kernel(name):
-    # multi-piece splines run a piece-binned kernel by default; the handle option "binned" = 0
-    # selects the plain one: same sums in the same order, so the results agree exactly
+    # multi-piece splines with much divergent work run a piece-binned kernel by default
+    # (interp_info_t.binned); the handle option "binned" selects either: the plain kernel shares
+    # the loads and the Horner evaluation between the pieces, but each piece's sums run in the
+    # same order, so the results agree exactly
     n_axis, nq = SMALL[name]
     sp, lat, xi, detl = spline_setup(name)
     dims = (n_axis,) * xi.shape[0]
     torch, itp = _interp(name, dims)
+    assert itp.info.binned == (name in ("d4s_8dir", "d4_8dir", "bcc_voronoi1", "fcc_voronoi2", "bcc_voronoi2"))
     itp.set_coeffs(torch.from_numpy(_coeffs(name, dims, 15)).cuda())
     pts = torch.from_numpy(mixed_points(name, dims, 5000, 16)).cuda()
     g = torch.linspace(-1, 1, pts.shape[0], device="cuda")
