@@ -761,8 +761,9 @@ __device__ __forceinline__ void eval_point(const float (&x)[SP::S], const DevVol
 }
 
 // MODE 0: out = f.  MODE 1: out = f (if out), grad = grad f.  MODE 2: grad = gout * grad f.
-template <class SP, class CT, int MODE>
-__global__ void __launch_bounds__(128) k_eval(const float *__restrict__ pts, int64_t n, DevVol<CT> v,
+// MINB: resident CTAs per SM the register allocation must allow (1: no bound)
+template <class SP, class CT, int MODE, int MINB = 1>
+__global__ void __launch_bounds__(128, MINB) k_eval(const float *__restrict__ pts, int64_t n, DevVol<CT> v,
                                               float *__restrict__ out, float *__restrict__ grad,
                                               const float *__restrict__ gout)
 {

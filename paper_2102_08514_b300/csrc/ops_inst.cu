@@ -43,6 +43,18 @@ constexpr int nnz_sum()
     return t;
 }
 
+// CTA residency the plain evaluation kernel's registers are fitted to.  One-piece splines with
+// wide stencils and the one-pass accumulation of b (>= 48 sites, <= 120 monomials: CC
+// 7-direction) get up to 128 registers (4 CTAs per SM): a query's gathers issue closer together
+// and its sectors are reused in L1 before they are evicted (measured, CC 7-direction on 256^3,
+// 2^24 random queries: 26.3 -> 18.7 L1 misses per query for its 15.0 distinct sectors, value
+// 1.563 -> 1.278 ms; spatially sorted queries 0.64 -> 0.70 ms).  The others are unbounded (the
+// compiler's choice, 55-72 registers; CC V_3's blocked accumulation measured no faster).
+constexpr int eval_min_blocks()
+{
+    return (SP::K == 1 && SP::NSMAX >= 48 && SP::NMON <= 120) ? 4 : 1;
+}
+
 // whether the piece-binned kernels are the default for evaluation (GRAD: value + gradient).
 // Sorting a tile's items by piece pays when the pieces' divergent work is large: the plain kernel
 // shares all but the accumulation of b between the pieces, so a warp pays the sum of the pieces'
@@ -135,7 +147,8 @@ template <class CT, int MODE>
 cudaError_t launch_eval(const float *pts, int64_t n, const void *c, const ibl::Layout &L, float *out, float *grad,
                         const float *gout, int, cudaStream_t st)
 {
-    ib::k_eval<SP, CT, MODE><<<grid_for(n), kTPB, 0, st>>>(pts, n, make_vol<CT>(c, L), out, grad, gout);
+    ib::k_eval<SP, CT, MODE, eval_min_blocks()><<<grid_for(n), kTPB, 0, st>>>(pts, n, make_vol<CT>(c, L), out, grad,
+                                                                               gout);
     return cudaPeekAtLastError();
 }
 

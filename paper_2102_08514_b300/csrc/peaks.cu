@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace {
 
 // FMA chains: NCH independent accumulators per thread, ITER rounds of NCH FMAs each
@@ -149,29 +151,25 @@ __global__ void __launch_bounds__(128) k_red(float *__restrict__ buf, uint32_t m
     }
 }
 
-// shared-memory atomics: 8 per thread and round at pseudo-random words of a 16 KiB block-local
-// array, float add (T = 0) or 32-bit integer add (T = 1)
+// shared-memory atomics: 8 per thread and round at pseudo-random elements of a 4096-element
+// block-local array: float add (T = 0), 32-bit integer add (T = 1), 64-bit integer add (T = 2)
 template <int T>
 __global__ void __launch_bounds__(256) k_shared_atomic(int iters, float *__restrict__ out)
 {
-    __shared__ float sf[4096];
-    __shared__ unsigned su[4096];
-    for (int i = threadIdx.x; i < 4096; i += blockDim.x) {
-        sf[i] = 0.0f;
-        su[i] = 0u;
-    }
+    using E = std::conditional_t<T == 0, float, std::conditional_t<T == 1, unsigned, unsigned long long>>;
+    __shared__ E sa[4096];
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x) sa[i] = E(0);
     __syncthreads();
     uint32_t st = lcg(blockIdx.x * blockDim.x + threadIdx.x);
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             st = lcg(st);
-            if constexpr (T == 0) atomicAdd(&sf[(st >> 8) & 4095u], 1.0f);
-            else atomicAdd(&su[(st >> 8) & 4095u], 1u);
+            atomicAdd(&sa[(st >> 8) & 4095u], E(1));
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) out[blockIdx.x] = sf[threadIdx.x] + (float)su[threadIdx.x];
+    if (threadIdx.x == 0) out[blockIdx.x] = (float)sa[threadIdx.x];
 }
 
 }  // namespace
@@ -226,13 +224,15 @@ int peaks_red(float *buf, uint32_t mask, int grid, int iters, void *stream)
     return (int)cudaPeekAtLastError();
 }
 
-// shared-memory atomics: count = grid * 256 * 8 * iters; type 0 float add, 1 integer add.  `out`
+// shared-memory atomics: count = grid * 256 * 8 * iters; type 0 float add, 1 32-bit integer add,
+// 2 64-bit integer add.  `out`
 // (grid floats) receives one value per CTA.
 int peaks_shared_atomic(int type, int grid, int iters, float *out, void *stream)
 {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (type == 0) k_shared_atomic<0><<<grid, 256, 0, st>>>(iters, out);
     else if (type == 1) k_shared_atomic<1><<<grid, 256, 0, st>>>(iters, out);
+    else if (type == 2) k_shared_atomic<2><<<grid, 256, 0, st>>>(iters, out);
     else return (int)cudaErrorInvalidValue;
     return (int)cudaPeekAtLastError();
 }

@@ -17,8 +17,8 @@
   second when one L1 -> L2 request carries 1, 2 or 4 sectors;
 * ``red_gatomics_s`` -- red.global.add.f32 at pseudo-random addresses of an L2-resident buffer
   (the adjoint's scatter);
-* ``shared_atomic_{f32,u32}_gops_s`` -- shared-memory atomic adds at pseudo-random words, float
-  and integer (the binned adjoint's per-bin sums).
+* ``shared_atomic_{f32,u32,u64}_gops_s`` -- shared-memory atomic adds at pseudo-random elements:
+  float, 32- and 64-bit integer (the binned adjoint's per-bin sums).
 
 The SM count comes from the device; the caller samples the SM clock around the calls (the
 per-clock figures divide by it).
@@ -138,7 +138,7 @@ def measure(torch=None) -> dict:
     # shared-memory atomics, float and integer add: 8 CTAs of 256 threads per SM
     sgrid, siters = sms * 8, 64
     sout = torch.empty(sgrid, device="cuda")
-    for t, name in ((0, "shared_atomic_f32_gops_s"), (1, "shared_atomic_u32_gops_s")):
+    for t, name in ((0, "shared_atomic_f32_gops_s"), (1, "shared_atomic_u32_gops_s"), (2, "shared_atomic_u64_gops_s")):
         ms = _best_ms(torch, lambda: _check(lib.peaks_shared_atomic(t, sgrid, siters, ctypes.c_void_p(sout.data_ptr()), st),
                                             "peaks_shared_atomic"))
         res[name] = sgrid * 256 * 8 * siters / (ms * 1e-3) / 1e9
@@ -157,7 +157,8 @@ def per_clock(res: dict, sm_mhz: float) -> dict:
                for k, v in res.items() if k.endswith("_gloads_s")},
             "red_per_clk_per_sm": res["red_gatomics_s"] * 1e9 / (sms * hz),
             "shared_atomic_f32_per_clk_per_sm": res["shared_atomic_f32_gops_s"] * 1e9 / (sms * hz),
-            "shared_atomic_u32_per_clk_per_sm": res["shared_atomic_u32_gops_s"] * 1e9 / (sms * hz)}
+            "shared_atomic_u32_per_clk_per_sm": res["shared_atomic_u32_gops_s"] * 1e9 / (sms * hz),
+            "shared_atomic_u64_per_clk_per_sm": res["shared_atomic_u64_gops_s"] * 1e9 / (sms * hz)}
 
 
 if __name__ == "__main__":
