@@ -738,6 +738,13 @@ __device__ __forceinline__ void eval_point(const float (&x)[SP::S], const DevVol
             const auto f = fold_coset<SP, decltype(Kc)::value, CT>(x, v);
             if (f.in_range) eval_piece<SP, 0, GRAD, CT>(f, v, val, grad);
         });
+    } else if constexpr (SP::NMON <= 120 && (SP::K <= 6 || SP::NNZMAX <= 100) && SP::M * SP::NNZMAX <= 200) {
+        // several small pieces (FCC: 4 cosets x 3 pieces of <= 40 nonzeros): the coset loop
+        // unrolled as for one piece, the pieces sharing all code but the accumulation of b
+        sfor<SP::M>([&](auto Kc) {
+            const auto f = fold_coset<SP, decltype(Kc)::value, CT>(x, v);
+            if (f.in_range) eval_piece_shared<SP, GRAD, CT>(f, v, val, grad);
+        });
     } else {
         // several pieces: run-time coset loop; the pieces share all code but the accumulation of
         // b (monomial spaces up to 120; up to six pieces, or more with small A_j), else one copy of
