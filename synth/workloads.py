@@ -15,7 +15,7 @@ import numpy as np
 
 __all__ = ["LatticeSpec", "SplineSpec", "LATTICES", "SPLINES", "Workload", "WORKLOADS",
            "interior_box", "make_rng", "uniform_points", "coefficients", "marschner_lobb", "gaussian", "D4_GAUSS_SIGMA",
-           "site_positions", "ray_setup", "ray_points", "batch_volumes"]
+           "site_positions", "ray_setup", "ray_points", "batch_volumes", "hashed_coefficients"]
 
 SEED_BASE = 2102
 
@@ -192,6 +192,20 @@ def coefficients(wl: Workload, dtype=np.float32) -> np.ndarray:
     else:
         raise ValueError(wl.coeffs)
     return c.astype(dtype)
+
+
+def hashed_coefficients(k, idx, xp=np):
+    """Coefficient of coset k at integer site indices idx = (i_1, ..., i_s) (broadcastable int64
+    arrays of numpy, or of torch when xp is torch): an integer hash of the indices mapped to
+    multiples of 1/1024 in [-1, 1).  Exact in FP32 and computable for any slab of a volume too
+    large to generate at once; the same values from numpy and torch."""
+    mult = (73856093, 19349663, 83492791, 2654435761)
+    h = k * 40503
+    for a, i in enumerate(idx):
+        h = h ^ (i * mult[a])
+    if xp is np:
+        return ((np.asarray(h) & 2047) - 1024).astype(np.float32) / np.float32(1024.0)
+    return ((h & 2047) - 1024).to(xp.float32) / 1024.0
 
 
 # ----------------------------------------------------------------------------- rays

@@ -61,6 +61,11 @@ def test_create_argument_errors_without_gpu(lib):
     with pytest.raises(binding.InterpError) as e:
         binding.interp_create(np.eye(2, dtype=int), np.eye(2, dtype=int), (8, 8))
     assert e.value.status == binding.INTERP_EUNSUPPORTED
+    # padded FP32 arrays of 2 x 1024^3 elements (dims 1015^3 + halo, rounded to whole bricks)
+    # exceed the 32-bit element offsets: refused before any allocation (1014^3 fits, GPU test)
+    with pytest.raises(binding.InterpError) as e:
+        binding.interp_create(L, xi, (1015, 1015, 1015))
+    assert e.value.status == binding.INTERP_ESIZE
     h = binding.load()
     assert h.interp_eval(None, None, 0, None, None) == binding.INTERP_EINVAL
 

@@ -9,14 +9,16 @@ oracle, at the tolerances of the parity tests.
   the oracle's adjoint and central differences at that size;
 * D4*, 2 x 48^4 coefficients uniform in [-1, 1], 2^24 queries (value);
 * the 64-volume batch (edges log-uniform in 32..256, four splines, 2^20 queries each) plus the
-  D4* volume, one graph-replayed batched launch.
+  D4* volume, one graph-replayed batched launch;
+* the largest BCC quintic volume the 32-bit element offsets allow (2 x 1014^3), queries at both
+  corners.
 """
 import numpy as np
 import pytest
 
 import oracle
-from synth import (LATTICES, SPLINES, WORKLOADS, batch_volumes, coefficients, interior_box, make_rng, marschner_lobb,
-                   uniform_points)
+from synth import (LATTICES, SPLINES, WORKLOADS, batch_volumes, coefficients, hashed_coefficients, interior_box, make_rng,
+                   marschner_lobb, uniform_points)
 
 from _gpu_common import VALUE_TOL, OracleSpline, grad_bound, make_interpolator, require_cuda, spline_setup
 
@@ -171,3 +173,44 @@ def test_batch64_and_d4s_full_size_sampled():
         ref = OracleSpline(name).eval_sum(lat.D, lat.cosets, c, pts_h[idx])
         got = out.cpu().numpy()[idx]
         assert np.abs(got - ref).max() <= VALUE_TOL * np.abs(c).max(), (v, name)
+
+
+def test_bcc_quintic_largest_volume_both_corners():
+    """Maximum size: the largest cube of BCC quintic coefficients whose padded FP32 arrays fit the
+    library's 32-bit element offsets (2 x 1014^3 sites, 8.3 GB; 1015 is refused with ESIZE before
+    any allocation, test_abi), hashed coefficients generated on the device slab by slab.  Queries
+    near both corners and inside, value and gradient, each against the oracle on the block of
+    coefficients around it (shifted by a lattice vector; zero outside the volume)."""
+    torch = require_cuda()
+    name, n = "bcc_quintic", 1014
+    sp, lat, xi, detl = spline_setup(name)
+    dims = (n, n, n)
+    itp = make_interpolator(name, dims)
+    M = len(lat.cosets)
+    c = torch.empty((M,) + dims, device="cuda")
+    J = torch.arange(n, device="cuda", dtype=torch.int64)
+    for k in range(M):
+        for i0 in range(0, n, 64):
+            I = torch.arange(i0, min(n, i0 + 64), device="cuda", dtype=torch.int64)
+            c[k, i0:i0 + len(I)] = hashed_coefficients(k, (I[:, None, None], J[None, :, None], J[None, None, :]), xp=torch)
+    itp.set_coeffs(c)
+    del c
+    lo, hi = interior_box(name, dims)
+    rng = make_rng(3007, 0)
+    pts = np.concatenate([uniform_points(rng, 32, lo, lo + 4.0), uniform_points(rng, 32, hi - 4.0, hi),
+                          uniform_points(rng, 32, lo, hi)])
+    val, grad = itp.eval_grad(torch.from_numpy(pts).cuda())
+    val, grad = val.cpu().numpy(), grad.cpu().numpy()
+    o = oracle.Spline(xi, detl)
+    G = grad_bound(name, pts)
+    B = 10
+    for q, x in enumerate(pts.astype(np.float64)):
+        i0 = np.floor(x / lat.D).astype(np.int64) - 4
+        idx = [np.arange(i0[a], i0[a] + B) for a in range(3)]
+        blk = np.stack([hashed_coefficients(k, (idx[0][:, None, None], idx[1][None, :, None], idx[2][None, None, :]))
+                        for k in range(M)]).astype(np.float64)
+        inside = [(v >= 0) & (v < n) for v in idx]
+        blk *= (inside[0][:, None, None] & inside[1][None, :, None] & inside[2][None, None, :])[None]
+        ref_v, ref_g = oracle.eval_sum(o, lat.D, lat.cosets, blk, (x - lat.D * i0)[None], grad=True)
+        assert abs(val[q] - ref_v[0]) <= VALUE_TOL, (q, x, val[q], ref_v[0])
+        assert np.abs(grad[q] - ref_g[0]).max() <= VALUE_TOL * G, (q, x, grad[q], ref_g[0])
