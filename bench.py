@@ -634,7 +634,11 @@ def run_ours(args):
                          # rate of random L1-hit gathers
                          "l1_lookups_per_query": info.lookups_per_query,
                          "l1_lookup_frac": info.lookups_per_query * n / (kern_ms * 1e-3) / (pk["gather4B_l1_gloads_s"] * 1e9)
-                         if form != "adjoint" else None}},
+                         if form != "adjoint" else None,
+                         # the same sectors as bytes through L2 (32 B each) against the measured
+                         # coalesced L2 read rate: the bandwidth roofline of the gathers
+                         "l2_gbs": sectors * 32 * n / (kern_ms * 1e-3) / 1e9 if sectors else None,
+                         "l2_frac": sectors * 32 * n / (kern_ms * 1e-3) / 1e9 / pk["l2_read_gbs"] if sectors else None}},
         "peaks": {k: pk[k] for k in ("sms", "fp32_tflops", "gather_gsectors_s", "gather4B_l1_gloads_s",
                                      "red_gatomics_s", "shared_atomic_f32_gops_s", "l2_read_gbs", "clocks")},
         "forms": {k: {"evals_per_s": (RAY_EVALS[0] if k.startswith("rays") else n) / (v * 1e-3), "ms": v}
