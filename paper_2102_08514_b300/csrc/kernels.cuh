@@ -517,15 +517,28 @@ __device__ __forceinline__ void unfold_grad(const Fold<S> &f, const float (&gy)[
 }
 
 // steps 4-5 for piece J: accumulate f (and grad f if GRAD) into the query's sums
+template <class SP, int J, bool GRAD>
+__device__ __forceinline__ void eval_piece_c(const Fold<SP::S> &f, const float (&c)[SP::NS[J]], float &val,
+                                             float (&grad)[SP::S]);
+
 template <class SP, int J, bool GRAD, class CT>
 __device__ __forceinline__ void eval_piece(const Fold<SP::S> &f, const DevVol<CT> &v, float &val, float (&grad)[SP::S])
+{
+    constexpr int NS = SP::NS[J];
+    const CT *cb = v.c + f.base;
+    float c[NS];
+    sfor<NS>([&](auto Mi) { c[Mi] = load_coef<CT>(cb + site_offset<SP, J, decltype(Mi)::value>(f)); });
+    eval_piece_c<SP, J, GRAD>(f, c, val, grad);
+}
+
+// steps 4-5 for piece J on its gathered coefficients c
+template <class SP, int J, bool GRAD>
+__device__ __forceinline__ void eval_piece_c(const Fold<SP::S> &f, const float (&c)[SP::NS[J]], float &val,
+                                             float (&grad)[SP::S])
 {
     constexpr int S = SP::S;
     constexpr int NS = SP::NS[J];
     constexpr int NM = SP::NMON;
-    const CT *cb = v.c + f.base;
-    float c[NS];
-    sfor<NS>([&](auto Mi) { c[Mi] = load_coef<CT>(cb + site_offset<SP, J, decltype(Mi)::value>(f)); });
     float t[S];
     sfor<S>([&](auto A) {
         constexpr float an = SP::ANCHOR[J][decltype(A)::value];
@@ -789,6 +802,140 @@ __global__ void __launch_bounds__(128, MINB) k_eval(const float *__restrict__ pt
     if (finite) {
         eval_point<SP, MODE != 0, CT>(x, v, val, g);
     } else {
+        val = __int_as_float(0x7fc00000);
+        sfor<S>([&](auto A) { g[A] = val; });
+    }
+    if constexpr (MODE == 0) {
+        out[q] = val;
+    } else if constexpr (MODE == 1) {
+        if (out) out[q] = val;
+        sfor<S>([&](auto A) { grad[q * S + A] = g[A]; });
+    } else {
+        const float w = gout[q];
+        sfor<S>([&](auto A) { grad[q * S + A] = w * g[A]; });
+    }
+}
+
+// Warp-cooperative gathers for one-piece splines (the random-query form of k_eval).  A lane
+// folds its query (steps 1-3) and writes the element offsets of its T = M x NS stencil sites to
+// its row of a per-warp shared-memory table (T <= 32); the warp then fetches the sites of one
+// query per load instruction (lane l: site l), writing each value over its offset, and each lane
+// reads its own row back for steps 4-5.  One load instruction then asks
+// for the sectors of one compact stencil, so an L1 -> L2 request carries all the sectors the
+// query needs in one 128-byte line (BCC quintic: 8.9 lines for 12.5 sectors per query), where a
+// load of 32 different queries makes one request per sector.  Sums in the order of k_eval: the
+// same results bit for bit.  Every lane of a warp takes part (lanes without a query fetch offset
+// 0), so the kernel has no early return.  A warp whose queries lie within 8 cells per axis
+// (spatially sorted queries: their sectors are L1 hits anyway) skips the table and runs k_eval's
+// per-lane gathers instead, without the table's shared-memory traffic.
+constexpr int kCoopCoherentCells = 7;   // coset-0 cell index range per axis of a coherent warp
+
+// the table path of k_eval_coop: steps 1-3 for every coset, the offsets to the lane's row, the
+// warp's rounds of gathers, steps 4-5 from the row (warp-synchronous: every lane of the warp).
+// Row q holds its 32 words in 16-byte chunks permuted by q mod 8 (chunk c at c ^ (q & 7)): a lane
+// writes and reads its row with 16-byte accesses and a round reads and writes one row across the
+// warp, both without bank conflicts.
+template <class SP, bool GRAD, class CT>
+__device__ __forceinline__ void eval_coop_gather(const float (&x)[SP::S], bool finite, const DevVol<CT> &v, int *wt,
+                                                 int lane, float &val, float (&g)[SP::S])
+{
+    constexpr int S = SP::S, M = SP::M, NS = SP::NS[0], T = M * NS;
+    static_assert(T <= 32, "one round of loads per query");
+    int4 *const row = reinterpret_cast<int4 *>(wt + lane * 32);
+    const int sw = lane & 7;
+    Fold<S> f[M];
+    bool use[M];
+    int o[32];
+    sfor<32>([&](auto Mi) { o[Mi] = 0; });
+    sfor<M>([&](auto Kc) {
+        constexpr int K = decltype(Kc)::value;
+        f[K] = fold_coset<SP, K, CT>(x, v);
+        use[K] = finite && f[K].in_range;
+        sfor<NS>([&](auto Mi) {
+            constexpr int m = decltype(Mi)::value;
+            o[K * NS + m] = use[K] ? f[K].base + site_offset<SP, 0, m>(f[K]) : 0;
+        });
+    });
+    sfor<8>([&](auto Cc) {
+        constexpr int c = decltype(Cc)::value;
+        row[c ^ sw] = make_int4(o[4 * c], o[4 * c + 1], o[4 * c + 2], o[4 * c + 3]);
+    });
+    __syncwarp();
+    // round r: the sites of the warp's query r, lane l taking site l.  All offsets are read
+    // before any value is written back, so the 32 loads are in flight together.
+    if (lane < T) {
+        // the 8 column positions of lane l (rows r and r + 8 permute alike)
+        int *col[8];
+        sfor<8>([&](auto Kc) { col[Kc] = wt + ((lane ^ (decltype(Kc)::value << 2)) & 31); });
+        int off[32];
+        sfor<32>([&](auto Rc) {
+            constexpr int r = decltype(Rc)::value;
+            off[r] = col[r & 7][r * 32];
+        });
+        float cw[32];
+        sfor<32>([&](auto Rc) { cw[Rc] = load_coef<CT>(v.c + off[Rc]); });
+        sfor<32>([&](auto Rc) {
+            constexpr int r = decltype(Rc)::value;
+            col[r & 7][r * 32] = __float_as_int(cw[r]);
+        });
+    }
+    __syncwarp();
+    float cv[32];
+    sfor<8>([&](auto Cc) {
+        constexpr int c = decltype(Cc)::value;
+        const int4 w = row[c ^ sw];
+        cv[4 * c] = __int_as_float(w.x);
+        cv[4 * c + 1] = __int_as_float(w.y);
+        cv[4 * c + 2] = __int_as_float(w.z);
+        cv[4 * c + 3] = __int_as_float(w.w);
+    });
+    sfor<M>([&](auto Kc) {
+        constexpr int K = decltype(Kc)::value;
+        if (use[K]) {
+            float c[NS];
+            sfor<NS>([&](auto Mi) { c[Mi] = cv[K * NS + decltype(Mi)::value]; });
+            eval_piece_c<SP, 0, GRAD>(f[K], c, val, g);
+        }
+    });
+    __syncwarp();      // the rows are free for the next use
+}
+
+template <class SP, class CT, int MODE, int MINB = 1>
+__global__ void __launch_bounds__(128, MINB) k_eval_coop(const float *__restrict__ pts, int64_t n, DevVol<CT> v,
+                                                         float *__restrict__ out, float *__restrict__ grad,
+                                                         const float *__restrict__ gout)
+{
+    static_assert(SP::K == 1, "cooperative gathers need one stencil for every folded query");
+    constexpr int S = SP::S;
+    __shared__ __align__(16) int table[4][32 * 32];
+    const int lane = threadIdx.x & 31;
+    int *const wt = table[threadIdx.x >> 5];
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = q < n;
+    float x[S];
+    bool finite = live;
+    sfor<S>([&](auto A) {
+        x[A] = live ? pts[q * S + A] : 0.0f;
+        finite &= isfinite(x[A]);
+    });
+    float val = 0.0f;
+    float g[S];
+    sfor<S>([&](auto A) { g[A] = 0.0f; });
+    // the warp's extent in coset-0 cells (lanes without a finite query are neutral)
+    bool coherent = true;
+    sfor<S>([&](auto A) {
+        const int cell = finite ? __float2int_rd(x[A] * (1.0f / SP::D)) : 0;
+        const int lo = __reduce_min_sync(0xffffffffu, finite ? cell : 0x7fffffff);
+        const int hi = __reduce_max_sync(0xffffffffu, finite ? cell : -0x7fffffff - 1);
+        coherent &= (long long)hi - lo <= kCoopCoherentCells;
+    });
+    if (coherent) {
+        if (finite) eval_point<SP, MODE != 0, CT>(x, v, val, g);
+    } else {
+        eval_coop_gather<SP, MODE != 0, CT>(x, finite, v, wt, lane, val, g);
+    }
+    if (!live) return;
+    if (!finite) {
         val = __int_as_float(0x7fc00000);
         sfor<S>([&](auto A) { g[A] = val; });
     }

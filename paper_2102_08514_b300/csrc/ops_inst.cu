@@ -55,6 +55,25 @@ constexpr int eval_min_blocks()
     return (SP::K == 1 && SP::NSMAX >= 48 && SP::NMON <= 120) ? 4 : 1;
 }
 
+// whether the plain evaluation runs the warp-cooperative gathers (k_eval_coop): one-piece
+// splines with 24 to 32 stencil sites per query (all cosets), whose sites fill most of one load
+// instruction of a warp.  Measured, 2^24 random queries: BCC quintic (32 sites) value 0.822 ->
+// 0.673 ms, value + grad 0.878 -> 0.780 ms (L1 -> L2 requests 13.0 -> 9.1 per query); CC
+// 7-direction (53 sites, two rounds per query) value 1.278 -> 1.337 ms (the table's shared-
+// memory traffic outweighs the fewer requests), so longer stencils keep k_eval.
+constexpr bool coop_eval()
+{
+    return SP::K == 1 && SP::M * SP::NS[0] >= 24 && SP::M * SP::NS[0] <= 32;
+}
+
+// resident CTAs per SM the cooperative kernel's registers are fitted to: 8 for values (64
+// registers), 6 with the gradient (80 registers; at 64 it spills)
+template <int MODE>
+constexpr int coop_min_blocks()
+{
+    return MODE == 0 ? 8 : 6;
+}
+
 // whether the piece-binned kernels are the default for evaluation (GRAD: value + gradient).
 // Sorting a tile's items by piece pays when the pieces' divergent work is large: the plain kernel
 // shares all but the accumulation of b between the pieces, so a warp pays the sum of the pieces'
@@ -147,8 +166,12 @@ template <class CT, int MODE>
 cudaError_t launch_eval(const float *pts, int64_t n, const void *c, const ibl::Layout &L, float *out, float *grad,
                         const float *gout, int, cudaStream_t st)
 {
-    ib::k_eval<SP, CT, MODE, eval_min_blocks()><<<grid_for(n), kTPB, 0, st>>>(pts, n, make_vol<CT>(c, L), out, grad,
-                                                                               gout);
+    if constexpr (coop_eval())
+        ib::k_eval_coop<SP, CT, MODE, coop_min_blocks<MODE>()><<<grid_for(n), kTPB, 0, st>>>(pts, n, make_vol<CT>(c, L),
+                                                                                               out, grad, gout);
+    else
+        ib::k_eval<SP, CT, MODE, eval_min_blocks()><<<grid_for(n), kTPB, 0, st>>>(pts, n, make_vol<CT>(c, L), out,
+                                                                                   grad, gout);
     return cudaPeekAtLastError();
 }
 
