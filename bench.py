@@ -123,12 +123,14 @@ def brick_lb(s, esz, M, a):
     return lb
 
 
-def distinct_sectors_per_query(spline: str, pts, esz: int = 4):
+def distinct_sectors_per_query(spline: str, pts, esz: int = 4, dims=None):
     """Mean number of distinct 32-byte sectors (bricks) a query's coefficient gathers touch: the
     gather work of one query in the library's bricked layout, which bounds random queries (each
-    distinct sector is one L1 miss and one L1 -> L2 request).  3-D box splines (one stencil per
-    piece); None otherwise.  Follows the kernels' steps: nearest coset site, |y| sorted descending
-    (signed permutation), the piece from the plane bits through sigma, the piece's stencil."""
+    distinct sector is one L1 miss and one L1 -> L2 request).  With dims: the mean number of
+    distinct 128-byte lines instead (one request each when the query's sites share a load
+    instruction, as in the warp-cooperative gathers).  3-D box splines (one stencil per piece);
+    None otherwise.  Follows the kernels' steps: nearest coset site, |y| sorted descending (signed
+    permutation), the piece from the plane bits through sigma, the piece's stencil."""
     import json as _json
     from fractions import Fraction
     with open(os.path.join(ROOT, "paper_2102_08514_b300", "csrc", "generated", "splines.json")) as f:
@@ -162,10 +164,17 @@ def distinct_sectors_per_query(spline: str, pts, esz: int = 4):
         for A in range(3):
             ax = order[:, A]
             P[rows, :, ax] += (sg[rows, ax][:, None] * site[:, :, A])
-        b = np.zeros(P.shape[:2], dtype=np.int64)
-        for a in range(3):
-            b = b * 4096 + (P[..., a] >> lbs[a])
-        keys.append(b + (k << 40))
+        if dims is None:
+            b = np.zeros(P.shape[:2], dtype=np.int64)
+            for a in range(3):
+                b = b * 4096 + (P[..., a] >> lbs[a])
+            keys.append(b + (k << 40))
+        else:
+            # bricks in row-major order of the padded coset array (csrc/layout.h), the last
+            # axis fastest; cosets one after another; a line is 128 / 32 = 4 bricks
+            nb = [(((dims[a] + 4 * H + (1 << lbs[a]) - 1) >> lbs[a])) for a in range(3)]
+            blin = ((P[..., 0] >> lbs[0]) * nb[1] + (P[..., 1] >> lbs[1])) * nb[2] + (P[..., 2] >> lbs[2])
+            keys.append((k * nb[0] * nb[1] * nb[2] + blin) >> 2)
     K = np.sort(np.concatenate(keys, axis=1), axis=1)
     return float((1 + (np.diff(K, axis=1) != 0).sum(axis=1)).mean())
 
@@ -238,10 +247,10 @@ class ClockSampler:
 
 
 def recorded_capture(kernel: str):
-    """(DRAM bytes per launch, binding-resource fraction) from the last ncu capture of the kernel
-    (profiles/traffic.txt), or (None, None) when the library sources changed since that capture.
-    The binding resource of the random-query gather is the L1 -> L2 miss-request path
-    (l1tex__m_l1tex2xbar_req_cycles_active, fraction of its peak)."""
+    """(DRAM bytes per launch, L1 -> L2 request-cycle fraction, L1 data-pipe wavefront fraction)
+    from the last ncu capture of the kernel (profiles/traffic.txt), or Nones when the library
+    sources changed since that capture (l1tex__m_l1tex2xbar_req_cycles_active and
+    l1tex__data_pipe_lsu_wavefronts, fractions of their peaks)."""
     from paper_2102_08514_b300 import build as b
     digest = b.kernel_digest()[:16]
     try:
@@ -249,10 +258,11 @@ def recorded_capture(kernel: str):
             for line in f:
                 parts = line.split()
                 if len(parts) >= 3 and parts[0] == kernel and parts[1] == digest:
-                    return int(parts[2]), (float(parts[3]) if len(parts) > 3 else None)
+                    return (int(parts[2]), float(parts[3]) if len(parts) > 3 else None,
+                            float(parts[4]) if len(parts) > 4 else None)
     except OSError:
         pass
-    return None, None
+    return None, None, None
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -577,10 +587,16 @@ def run_ours(args):
     achieved = flops_per_launch / (kern_ms * 1e-3) / 1e12
     pk = measured_peaks(torch)
     peak = pk["fp32_tflops"]
-    kname = f"k_eval<{wl.spline},{args.storage},{form}>" if form != "adjoint" else f"k_adjoint<{wl.spline}>"
-    traffic, l1l2_frac = recorded_capture(kname)
+    kname = (f"{'k_eval_coop' if info.coop else 'k_eval'}<{wl.spline},{args.storage},{form}>" if form != "adjoint"
+             else f"k_adjoint<{wl.spline}>")
+    traffic, l1l2_frac, l1_pipe_frac = recorded_capture(kname)
     esz = 4 if args.storage == "f32" else 2
     sectors = distinct_sectors_per_query(wl.spline, pts_h[:1 << 16], esz) if form != "adjoint" else None
+    # L1 -> L2 requests per query: one per distinct sector when every lane gathers its own
+    # query, one per distinct 128-byte line when a load instruction holds one query's sites
+    lines = (distinct_sectors_per_query(wl.spline, pts_h[:1 << 16], esz, dims=wl.dims)
+             if form != "adjoint" and info.coop else None)
+    requests = lines if lines else sectors
     presort = presort_applies(info, n)
     if presort:
         kname += " after the piece pre-sort (whole call timed)"
@@ -619,17 +635,23 @@ def run_ours(args):
                                    "the Horner steps on structurally nonzero data, summed over the cosets), 2 FLOP each",
                      "peak_note": f"FP32 FMA rate measured in this run (peaks_fma microbenchmark, "
                                   f"{pk['sms']} SMs, SM clock {pk['clocks']['sm_mhz']} MHz), of measured",
-                     # random queries are bound by the coefficient gathers in L1TEX, not the FP32
-                     # pipe: the distinct sectors a query touches against the measured rate of
-                     # random sector gathers (one L1 miss request each)
+                     # random queries: the coefficient gathers in L1TEX beside the FP32 pipe: the
+                     # L1 -> L2 requests a query makes against the measured rate of random
+                     # one-sector requests (0.99 per SM clock)
                      "binding_resource": {
-                         "name": "coefficient gathers: distinct 32-byte sectors per query (L1 miss requests)",
+                         "name": ("coefficient gathers: L1 -> L2 requests per query (distinct 128-byte lines: "
+                                  "one query's sites per load instruction)" if lines else
+                                  "coefficient gathers: L1 -> L2 requests per query (distinct 32-byte sectors)"),
                          "sectors_per_query": sectors,
-                         "achieved_gsectors_s": sectors * n / (kern_ms * 1e-3) / 1e9 if sectors else None,
-                         "peak_gsectors_s": pk["gather_gsectors_s"],
-                         "frac": sectors * n / (kern_ms * 1e-3) / 1e9 / pk["gather_gsectors_s"] if sectors else None,
-                         "peak_note": "random 4-byte gathers from a 16 MiB L2-resident buffer, measured in this run",
+                         "lines_per_query": lines,
+                         "requests_per_query": requests,
+                         "achieved_grequests_s": requests * n / (kern_ms * 1e-3) / 1e9 if requests else None,
+                         "peak_grequests_s": pk["gather_gsectors_s"],
+                         "frac": requests * n / (kern_ms * 1e-3) / 1e9 / pk["gather_gsectors_s"] if requests else None,
+                         "peak_note": "random 4-byte gathers from a 16 MiB L2-resident buffer (one request each), "
+                                      "measured in this run",
                          "ncu_l1_to_l2_request_cycles_frac": l1l2_frac,
+                         "ncu_l1_data_pipe_wavefronts_frac": l1_pipe_frac,
                          # every coefficient is one L1 lookup (hit or miss): against the measured
                          # rate of random L1-hit gathers
                          "l1_lookups_per_query": info.lookups_per_query,

@@ -133,6 +133,8 @@ typedef struct {
                                   /*    default (see the conventions above)                 */
     int binned;                   /* 1: evaluation runs the piece-binned kernels by default  */
                                   /*    (>= 4 pieces with >= 200 nonzeros of A_j in all)     */
+    int coop;                     /* 1: evaluation gathers one query's stencil per warp load */
+                                  /*    instruction (one piece, 24 to 32 sites per query)    */
 } interp_info_t;
 interp_status interp_info(const interp_t *h, interp_info_t *info);
 

@@ -37,7 +37,7 @@ class InterpInfo(ctypes.Structure):
                 ("lookups_per_query", ctypes.c_double), ("fma_value_per_query", ctypes.c_double),
                 ("fma_grad_per_query", ctypes.c_double), ("coeff_count", ctypes.c_int64),
                 ("name", ctypes.c_char_p), ("kind", ctypes.c_int), ("presort", ctypes.c_int),
-                ("binned", ctypes.c_int)]
+                ("binned", ctypes.c_int), ("coop", ctypes.c_int)]
 
 
 class Rays(ctypes.Structure):

@@ -1170,6 +1170,7 @@ interp_status interp_info(const interp_t *h, interp_info_t *info)
     info->kind = o.kind;
     info->presort = presort_default(&o) ? 1 : 0;
     info->binned = o.binned_eval ? 1 : 0;
+    info->coop = o.coop_eval ? 1 : 0;
     return INTERP_OK;
 }
 

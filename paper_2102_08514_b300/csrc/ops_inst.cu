@@ -345,6 +345,7 @@ void IB_CAT(fill_, INTERP_SPLINE, _, INTERP_PART)(SplineOps &o)
     o.lookups = SP::LOOKUPS;
     o.nnz_sum = nnz_sum();
     o.binned_eval = binned_default<false, false>();
+    o.coop_eval = coop_eval();
     o.adjoint = launch_adjoint;
     if constexpr (SP::S == 3 && SP::K < 4 && SP::D <= 2) {
         o.adjoint_box = launch_adjoint_box;

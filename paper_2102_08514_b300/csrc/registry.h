@@ -49,6 +49,7 @@ struct SplineOps {
     int nnz_sum = 0;             // nonzeros of A_j summed over the pieces (a coset's divergent
                                  // work in a warp that meets every piece)
     bool binned_eval = false;    // evaluation defaults to the piece-binned kernels
+    bool coop_eval = false;      // evaluation runs the warp-cooperative gathers
     EvalFn eval[3][3] = {};      // [storage: f32, f16, bf16][mode: value, value+grad, pullback]
     EvalFn eval_binned[3][3] = {};  // the same, piece-binned (multi-piece splines only)
     AdjFn adjoint = nullptr;

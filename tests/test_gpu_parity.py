@@ -287,6 +287,35 @@ def test_piece_binned_kernel_equals_plain_kernel(name):
         assert torch.equal(torch.nan_to_num(a, nan=7.0), torch.nan_to_num(b, nan=7.0))
 
 
+@pytest.mark.parametrize("name", ["bcc_quintic", "bcc_quartic", "cc_voronoi2"])
+def test_cooperative_gathers_equal_per_lane_gathers(name):
+    # one-piece splines of 24 to 32 sites gather, for a warp of random queries, one query's
+    # stencil per load instruction through a shared-memory table, and per lane when the warp's
+    # queries lie within 8 cells per axis (here: the same queries spatially sorted); the sums run
+    # in the same order either way, so values, gradients and pullbacks agree bit for bit
+    sp, lat, xi, detl = spline_setup(name)
+    dims = (24,) * xi.shape[0]
+    torch, itp = _interp(name, dims)
+    assert itp.info.coop == 1
+    itp.set_coeffs(torch.from_numpy(_coeffs(name, dims, 41)).cuda())
+    pts = torch.from_numpy(mixed_points(name, dims, 20011, 42)).cuda()
+    perm, pts_s = itp.sort_points(pts)
+    perm = perm.long()
+    assert torch.equal(pts[perm], pts_s)
+    g = torch.linspace(-1, 1, pts.shape[0], device="cuda")
+    from paper_2102_08514_b300.binding import interp_backward
+    res = []
+    for p, gg in ((pts, g), (pts_s, g[perm])):
+        v = itp.eval(p)
+        v2, gr = itp.eval_grad(p)
+        dp = torch.empty_like(gr)
+        interp_backward(itp.handle, p, gg, None, dp)      # dcoeffs = NULL: the pullback only
+        res.append((v, v2, gr, dp))
+    for a, b in zip(res[0], res[1]):
+        assert torch.equal(torch.nan_to_num(a[perm], nan=7.0), torch.nan_to_num(b, nan=7.0))
+    assert _interp("cc_7dir", (8, 8, 8))[1].info.coop == 0 and _interp("fcc_6dir", (8, 8, 8))[1].info.coop == 0
+
+
 def test_named_creation_matches_lattice_and_directions():
     # interp_create_named reaches the same tables as interp_create for a box spline; a Voronoi
     # spline's recorded generators never match a direction-matrix request
