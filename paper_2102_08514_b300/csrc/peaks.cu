@@ -153,6 +153,36 @@ __global__ void __launch_bounds__(128) k_red(float *__restrict__ buf, uint32_t m
 
 // shared-memory atomics: 8 per thread and round at pseudo-random elements of a 4096-element
 // block-local array: float add (T = 0), 32-bit integer add (T = 1), 64-bit integer add (T = 2)
+// T = 3: a 64-bit fixed-point sum kept as two 32-bit words: the low word by an integer add that
+// returns the old value, the high word only when the value's high part plus the carry is not
+// zero (values +-0.75 scaled by 2^40, alternating in sign)
+__global__ void __launch_bounds__(256) k_shared_fixed(int iters, float *__restrict__ out)
+{
+    __shared__ unsigned slo[4096];
+    __shared__ int shi[4096];
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x) {
+        slo[i] = 0u;
+        shi[i] = 0;
+    }
+    __syncthreads();
+    uint32_t st = lcg(blockIdx.x * blockDim.x + threadIdx.x);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            st = lcg(st);
+            const float v = (st & 256u) ? -0.75f : 0.75f;
+            const long long q = __float2ll_rn(v * 0x1p40f);
+            const unsigned lo = (unsigned)q;
+            const unsigned e = (st >> 8) & 4095u;
+            const unsigned old = atomicAdd(&slo[e], lo);
+            const int hi = (int)(q >> 32) + (old + lo < old ? 1 : 0);
+            if (hi != 0) atomicAdd(&shi[e], hi);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) out[blockIdx.x] = (float)slo[0] + (float)shi[0];
+}
+
 template <int T>
 __global__ void __launch_bounds__(256) k_shared_atomic(int iters, float *__restrict__ out)
 {
@@ -225,7 +255,7 @@ int peaks_red(float *buf, uint32_t mask, int grid, int iters, void *stream)
 }
 
 // shared-memory atomics: count = grid * 256 * 8 * iters; type 0 float add, 1 32-bit integer add,
-// 2 64-bit integer add.  `out`
+// 2 64-bit integer add, 3 64-bit fixed-point add as two 32-bit words.  `out`
 // (grid floats) receives one value per CTA.
 int peaks_shared_atomic(int type, int grid, int iters, float *out, void *stream)
 {
@@ -233,6 +263,7 @@ int peaks_shared_atomic(int type, int grid, int iters, float *out, void *stream)
     if (type == 0) k_shared_atomic<0><<<grid, 256, 0, st>>>(iters, out);
     else if (type == 1) k_shared_atomic<1><<<grid, 256, 0, st>>>(iters, out);
     else if (type == 2) k_shared_atomic<2><<<grid, 256, 0, st>>>(iters, out);
+    else if (type == 3) k_shared_fixed<<<grid, 256, 0, st>>>(iters, out);
     else return (int)cudaErrorInvalidValue;
     return (int)cudaPeekAtLastError();
 }

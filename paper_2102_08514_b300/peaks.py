@@ -18,7 +18,8 @@
 * ``red_gatomics_s`` -- red.global.add.f32 at pseudo-random addresses of an L2-resident buffer
   (the adjoint's scatter);
 * ``shared_atomic_{f32,u32,u64}_gops_s`` -- shared-memory atomic adds at pseudo-random elements:
-  float, 32- and 64-bit integer (the binned adjoint's per-bin sums).
+  float, 32- and 64-bit integer (the binned adjoint's per-bin sums); ``shared_fixed64_gops_s``
+  a 64-bit fixed-point add kept as two 32-bit words (low word with carry out).
 
 The SM count comes from the device; the caller samples the SM clock around the calls (the
 per-clock figures divide by it).
@@ -138,7 +139,8 @@ def measure(torch=None) -> dict:
     # shared-memory atomics, float and integer add: 8 CTAs of 256 threads per SM
     sgrid, siters = sms * 8, 64
     sout = torch.empty(sgrid, device="cuda")
-    for t, name in ((0, "shared_atomic_f32_gops_s"), (1, "shared_atomic_u32_gops_s"), (2, "shared_atomic_u64_gops_s")):
+    for t, name in ((0, "shared_atomic_f32_gops_s"), (1, "shared_atomic_u32_gops_s"), (2, "shared_atomic_u64_gops_s"),
+                    (3, "shared_fixed64_gops_s")):
         ms = _best_ms(torch, lambda: _check(lib.peaks_shared_atomic(t, sgrid, siters, ctypes.c_void_p(sout.data_ptr()), st),
                                             "peaks_shared_atomic"))
         res[name] = sgrid * 256 * 8 * siters / (ms * 1e-3) / 1e9
