@@ -247,10 +247,11 @@ class ClockSampler:
 
 
 def recorded_capture(kernel: str):
-    """(DRAM bytes per launch, L1 -> L2 request-cycle fraction, L1 data-pipe wavefront fraction)
-    from the last ncu capture of the kernel (profiles/traffic.txt), or Nones when the library
-    sources changed since that capture (l1tex__m_l1tex2xbar_req_cycles_active and
-    l1tex__data_pipe_lsu_wavefronts, fractions of their peaks)."""
+    """(DRAM bytes per launch, L1 -> L2 request-cycle fraction, L1 data-pipe wavefront fraction,
+    warp instructions per launch) from the last ncu capture of the kernel (profiles/traffic.txt),
+    or Nones when the library sources changed since that capture
+    (l1tex__m_l1tex2xbar_req_cycles_active and l1tex__data_pipe_lsu_wavefronts as fractions of
+    their peaks, smsp__inst_executed.sum)."""
     from paper_2102_08514_b300 import build as b
     digest = b.kernel_digest()[:16]
     try:
@@ -259,10 +260,10 @@ def recorded_capture(kernel: str):
                 parts = line.split()
                 if len(parts) >= 3 and parts[0] == kernel and parts[1] == digest:
                     return (int(parts[2]), float(parts[3]) if len(parts) > 3 else None,
-                            float(parts[4]) if len(parts) > 4 else None)
+                            float(parts[4]) if len(parts) > 4 else None, int(parts[5]) if len(parts) > 5 else None)
     except OSError:
         pass
-    return None, None, None
+    return None, None, None, None
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -589,7 +590,7 @@ def run_ours(args):
     peak = pk["fp32_tflops"]
     kname = (f"{'k_eval_coop' if info.coop else 'k_eval'}<{wl.spline},{args.storage},{form}>" if form != "adjoint"
              else f"k_adjoint<{wl.spline}>")
-    traffic, l1l2_frac, l1_pipe_frac = recorded_capture(kname)
+    traffic, l1l2_frac, l1_pipe_frac, warp_instr = recorded_capture(kname)
     esz = 4 if args.storage == "f32" else 2
     sectors = distinct_sectors_per_query(wl.spline, pts_h[:1 << 16], esz) if form != "adjoint" else None
     # L1 -> L2 requests per query: one per distinct sector when every lane gathers its own
@@ -652,6 +653,11 @@ def run_ours(args):
                                       "measured in this run",
                          "ncu_l1_to_l2_request_cycles_frac": l1l2_frac,
                          "ncu_l1_data_pipe_wavefronts_frac": l1_pipe_frac,
+                         # the issue roofline: the recorded warp instructions of one launch over
+                         # this run's kernel time, against 4 warp instructions per SM and clock
+                         "instructions_per_query": warp_instr * 32 / n if warp_instr else None,
+                         "issue_frac": (warp_instr / (kern_ms * 1e-3)
+                                        / (4 * pk["sms"] * pk["clocks"]["sm_mhz"] * 1e6)) if warp_instr else None,
                          # every coefficient is one L1 lookup (hit or miss): against the measured
                          # rate of random L1-hit gathers
                          "l1_lookups_per_query": info.lookups_per_query,
