@@ -1842,11 +1842,13 @@ constexpr int box_lb()
     return 3;
 }
 
-// resident CTAs per SM of the box kernel (256 threads): four where the registers allow it
+// resident CTAs per SM of the box kernel (256 threads): as many as the registers allow without
+// spilling (4 up to 32 sites; 3 for wider stencils with up to 120 monomials, CC 7-direction: 80
+// registers; 2 for CC V_3's 220 monomials)
 template <class SP>
 constexpr int box_min_blocks()
 {
-    return SP::NS[0] <= 32 ? 4 : 2;
+    return SP::NS[0] <= 32 ? 4 : (SP::NMON <= 120 ? 3 : 2);
 }
 
 template <class SP, int LB>
