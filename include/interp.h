@@ -190,7 +190,10 @@ interp_status interp_prefilter(interp_t *h, const float *samples, int ntaps, con
 /*
  * interp_eval -- out[q] = f(pts[q]) for q < npts (Sec. 4, Algorithm 1, per query: coset loop,
  * shift to the region of evaluation, symmetry fold, branch-free piece selection by plane sign
- * bits, coefficient gather, Horner evaluation in FP32 FMA).  npts = 0 is a no-op.
+ * bits, coefficient gather, Horner evaluation in FP32 FMA).  npts = 0 is a no-op.  For splines
+ * with interp_info_t.coop = 1 a warp gathers the stencil of one query per load instruction
+ * (16 KB of static shared memory per 128-thread block); the results are the same bits as with
+ * per-query gathers.
  */
 interp_status interp_eval(const interp_t *h, const float *pts, int64_t npts, float *out, void *stream);
 
