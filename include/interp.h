@@ -231,7 +231,7 @@ interp_status interp_eval_host(interp_t *h, const float *pts, int64_t npts, floa
  *     times; option "adjoint_bins" = 0 / 1 forces it off / on): the query indices are first
  *     counting-sorted on the device into spatial bins of 8^3 coset cells; each bin's contributions
  *     are summed in a shared-memory box and added to
- *     the padded buffer once per site.  The scratch (8 bytes per query plus 16 per bin) comes
+ *     the padded buffer once per site.  The scratch (24 bytes per query plus 16 per bin) comes
  *     from the library's stream-ordered pool (see the piece pre-sort); under stream capture, or
  *     when the pool has no room, the call takes the path below.
  *   - Otherwise, 3-D splines: each block of 1024 consecutive queries whose cells fit a small box

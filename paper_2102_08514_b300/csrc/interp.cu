@@ -656,7 +656,7 @@ constexpr int kBoxUnroll = 4;
 
 __global__ void __launch_bounds__(256) k_box_count(const float *__restrict__ pts, const float *__restrict__ gout, int n,
                                                    BoxGeom g, ibl::Layout L, unsigned *__restrict__ counts,
-                                                   int *__restrict__ keys)
+                                                   int *__restrict__ keys, float4 *__restrict__ rec)
 {
     __shared__ unsigned hist[kBoxSharedBins];
     const bool sh = g.nbins <= kBoxSharedBins;
@@ -670,8 +670,14 @@ __global__ void __launch_bounds__(256) k_box_count(const float *__restrict__ pts
 #pragma unroll
         for (int u = 0; u < kBoxUnroll; ++u) {
             const int q = qb + u * blockDim.x;
-            key[u] = q < q1 ? box_key(pts + (int64_t)q * 3, gout[q], g, L) : -1;
-            if (q < q1) keys[q] = key[u];
+            key[u] = -1;
+            if (q < q1) {
+                const float *p = pts + (int64_t)q * 3;
+                const float w = gout[q];
+                key[u] = box_key(p, w, g, L);
+                keys[q] = key[u];
+                rec[q] = make_float4(p[0], p[1], p[2], w);     // the query as one 16-byte record
+            }
         }
 #pragma unroll
         for (int u = 0; u < kBoxUnroll; ++u) {
@@ -862,7 +868,7 @@ static bool adjoint_box_launch(const interp *h, const BoxGeom &g, const float *p
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t nb = (size_t)g.nbins;
     const size_t sz[] = {up((size_t)n * 4), up((size_t)n * 4), up(nb * 4), up((nb + 1) * 4), up((nb + 1) * 4),
-                         up(nb * 4)};
+                         up(nb * 4), up((size_t)n * 16)};
     size_t bytes = 0;
     for (size_t b : sz) bytes += b;
     cudaMemPool_t pool = nullptr;
@@ -888,20 +894,21 @@ static bool adjoint_box_launch(const interp *h, const BoxGeom &g, const float *p
     int *item_start = reinterpret_cast<int *>(p);
     p += sz[4];
     unsigned *cursor = reinterpret_cast<unsigned *>(p);
+    p += sz[5];
+    float4 *rec = reinterpret_cast<float4 *>(p);
     cudaError_t e = cudaMemsetAsync(counts, 0, nb * 4, st);
     const unsigned grid = (unsigned)((n + kBoxBlock - 1) / kBoxBlock);
     const size_t scat_smem = g.nbins <= kBoxSharedBins ? 2 * nb * sizeof(unsigned) : 0;
     if (e == cudaSuccess && scat_smem > 48 * 1024) e = box_scatter_smem_optin(h->device);
     if (e == cudaSuccess) {
-        k_box_count<<<grid, 256, 0, st>>>(pts, gout, n, g, h->lay32, counts, keys);
+        k_box_count<<<grid, 256, 0, st>>>(pts, gout, n, g, h->lay32, counts, keys, rec);
         k_box_scan<<<1, 1024, 0, st>>>(counts, g.nbins, kBoxChunk, bin_start, item_start, cursor);
         k_box_scatter<<<grid, 256, scat_smem, st>>>(keys, n, g.nbins, cursor, idx);
         e = cudaPeekAtLastError();
     }
     if (e == cudaSuccess) {
         ibr::BoxArgs a;
-        a.pts = pts;
-        a.gout = gout;
+        a.rec = reinterpret_cast<const float *>(rec);
         a.idx = idx;
         a.bin_start = bin_start;
         a.item_start = item_start;

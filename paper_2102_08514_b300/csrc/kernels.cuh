@@ -1865,7 +1865,7 @@ struct BoxGrid {
 };
 
 template <class SP, int LB, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_adjoint_box(const float *__restrict__ pts, const float *__restrict__ gout,
+__global__ void __launch_bounds__(256, MINB) k_adjoint_box(const float4 *__restrict__ rec,
                                                         const int *__restrict__ idx, const int *__restrict__ bin_start,
                                                         const int *__restrict__ item_start, BoxGrid g, DevVol<float> v,
                                                         float *__restrict__ dpad)
@@ -1891,22 +1891,14 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint_box(const float *__restri
     constexpr int lstride[S] = {W * W, W, 1};
     for (int i = threadIdx.x; i < M * VOL; i += blockDim.x) sacc[i] = 0.0f;
     __syncthreads();
-    // the next query's point and gout are loaded one iteration ahead (random gathers: their
-    // latency hides behind the current query's work)
-    float nx[S] = {0.0f, 0.0f, 0.0f}, nw = 0.0f;
-    if (q0 + (int)threadIdx.x < q1) {
-        const int64_t q = idx[q0 + threadIdx.x];
-        sfor<S>([&](auto A) { nx[A] = pts[q * S + A]; });
-        nw = gout[q];
-    }
+    // the next query's record (x, y, z, gout: one 16-byte gather) is loaded one iteration ahead
+    // (random gathers: their latency hides behind the current query's work)
+    float4 nr = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (q0 + (int)threadIdx.x < q1) nr = rec[idx[q0 + threadIdx.x]];
     for (int i = q0 + threadIdx.x; i < q1; i += blockDim.x) {
-        const float x[S] = {nx[0], nx[1], nx[2]};
-        const float w = nw;
-        if (i + (int)blockDim.x < q1) {
-            const int64_t q = idx[i + blockDim.x];
-            sfor<S>([&](auto A) { nx[A] = pts[q * S + A]; });
-            nw = gout[q];
-        }
+        const float x[S] = {nr.x, nr.y, nr.z};
+        const float w = nr.w;
+        if (i + (int)blockDim.x < q1) nr = rec[idx[i + blockDim.x]];
         sfor<M>([&](auto Kc) {
             constexpr int K = decltype(Kc)::value;
             const auto f = fold_coset<SP, K, float>(x, v);

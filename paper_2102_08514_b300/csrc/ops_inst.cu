@@ -230,8 +230,8 @@ template <int LB, int MINB>
     g.nb[1] = a.nb[1];
     g.nb[2] = a.nb[2];
     g.chunk = a.chunk;
-    kern<<<(unsigned)a.max_items, 256, smem, st>>>(a.pts, a.gout, a.idx, a.bin_start, a.item_start, g,
-                                                    make_vol<float>(nullptr, L), dpad);
+    kern<<<(unsigned)a.max_items, 256, smem, st>>>(reinterpret_cast<const float4 *>(a.rec), a.idx, a.bin_start,
+                                                    a.item_start, g, make_vol<float>(nullptr, L), dpad);
     return cudaPeekAtLastError();
 }
 

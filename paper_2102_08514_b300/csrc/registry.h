@@ -26,11 +26,11 @@ using RayFn = cudaError_t (*)(const ibl::RayGeom &, const void *, const ibl::Lay
 using SortFn = cudaError_t (*)(const float *, int64_t, const ibl::Layout &, int, int, unsigned *, int, int32_t *,
                                float *, cudaStream_t);
 using DbgFn = cudaError_t (*)(const float *, int64_t, const ibl::Layout &, int32_t *, int32_t *, cudaStream_t);
-// the adjoint on spatially binned queries: the caller's points and gout, the query indices in
-// bin order, bin starts, work item starts, bins per axis and chunk, work items at most
+// the adjoint on spatially binned queries: the queries as 16-byte records (x, y, z, gout) in
+// the caller's order, the query indices in bin order, bin starts, work item starts, bins per
+// axis and chunk, work items at most
 struct BoxArgs {
-    const float *pts;
-    const float *gout;
+    const float *rec;
     const int *idx;
     const int *bin_start;
     const int *item_start;
