@@ -80,3 +80,32 @@ def test_distinct_sectors_match_the_support():
                     P = ii + 2 * H
                     keys.add((k,) + tuple(int(P[a]) >> lbs[a] for a in range(3)))
             assert bench.distinct_sectors_per_query(wl.spline, x[None].astype(np.float32)) == len(keys), (wname, x)
+
+
+def test_distinct_lines_match_the_support():
+    """The 128-byte line count (the requests of the warp-cooperative gathers) from the oracle's
+    support and the padded bricked layout written out: bricks of 2 x 2 x 2 FP32 sites in row-major
+    order of the padded coset array (last axis fastest), cosets one after another, 4 bricks per
+    line."""
+    import numpy as np
+    import oracle
+    from synth import LATTICES, SPLINES, WORKLOADS, interior_box, make_rng, uniform_points
+    wl = WORKLOADS["bcc_quintic_128"]
+    sp = SPLINES[wl.spline]
+    lat = LATTICES[sp.lattice]
+    o = oracle.Spline(np.asarray(sp.xi), abs(round(np.linalg.det(np.asarray(lat.L, dtype=float)))))
+    D, H = lat.D, 2
+    nb = [(n + 4 * H + 1) // 2 for n in wl.dims]         # bricks per axis of the padded array
+    lo, hi = interior_box(wl.spline, wl.dims)
+    pts = uniform_points(make_rng(7, 2), 16, lo, hi)
+    grid = np.stack(np.meshgrid(*[np.arange(-3, 4)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    for x in pts.astype(np.float64):
+        lines = set()
+        for k, l in enumerate(lat.cosets):
+            i = np.floor((x - l) / D).astype(np.int64) + grid
+            val = o.phi(x - (D * i + np.asarray(l)))
+            for ii in i[val != 0]:
+                b = (ii + 2 * H) // 2
+                lines.add((k * nb[0] * nb[1] * nb[2] + (b[0] * nb[1] + b[1]) * nb[2] + b[2]) // 4)
+        got = bench.distinct_sectors_per_query(wl.spline, x[None].astype(np.float32), dims=wl.dims)
+        assert got == len(lines), (x, got, len(lines))
