@@ -135,6 +135,105 @@ __global__ void __launch_bounds__(128) k_gather_lines(const float *__restrict__ 
     if (acc == 1234.5f) out[t] = acc;
 }
 
+// ---- tensor cores: tcgen05.mma kind::tf32, D[128 x 128] (+)= A[128 x 32] B[128 x 32]^T per CTA
+// Both operands K-major in shared memory with the 128-byte swizzle (16-byte chunk c of row r at
+// chunk c ^ (r mod 8), 8-row groups 1024 bytes apart), the accumulator in TMEM (128 lanes x 128
+// FP32 columns), completion tracked by an mbarrier with a bounded wait (err = 1 on time-out).
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t tc_desc_sw128(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);            // start address / 16
+    d |= (uint64_t)1 << 16;                             // leading byte offset (unused: K fits one row)
+    d |= (uint64_t)((1024 >> 4) & 0x3FFF) << 32;        // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                             // descriptor version
+    d |= (uint64_t)2 << 61;                             // 128-byte swizzle
+    return d;
+}
+
+// kind::tf32 instruction descriptor: FP32 accumulator, TF32 A and B, both K-major, M x N
+constexpr uint32_t tc_idesc_tf32(int M, int N)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// every CTA: iters x 4 MMAs of 128 x 128 x 8 accumulating one 128 x 128 x 32 product per
+// iteration; CTA 0 writes its accumulator to D (iters = 1: D = A B^T)
+__global__ void __launch_bounds__(128) k_tc_tf32(const float *__restrict__ A, const float *__restrict__ B,
+                                                 float *__restrict__ D, int iters, int *__restrict__ err)
+{
+    extern __shared__ __align__(1024) unsigned char tc_sm[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)tc_sm + 1023) & ~(uintptr_t)1023);
+    float *sA = (float *)base;
+    float *sB = (float *)(base + 16384);
+    uint64_t *mbar = (uint64_t *)(base + 32768);
+    uint32_t *taddr_s = (uint32_t *)(base + 32768 + 16);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < 128 * 32; i += 128) {
+        const int row = i >> 5, k = i & 31;
+        const int p = row * 32 + (((k >> 2) ^ (row & 7)) << 2) + (k & 3);
+        sA[p] = A[i];
+        sB[p] = B[i];
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(taddr_s)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t taddr = *taddr_s;
+    if (tid == 0) {
+        const uint32_t id = tc_idesc_tf32(128, 128);
+        for (int it = 0; it < iters; ++it) {
+            for (int k = 0; k < 4; ++k) {
+                const uint64_t da = tc_desc_sw128(smem_u32(sA) + k * 32);
+                const uint64_t db = tc_desc_sw128(smem_u32(sB) + k * 32);
+                const uint32_t acc = (it | k) ? 1u : 0u;
+                asm volatile("{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
+                             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                             ::"r"(taddr), "l"(da), "l"(db), "r"(id), "r"(acc));
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar)));
+    }
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 24) && !done; ++it)
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\nselp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done) : "r"(smem_u32(mbar)));
+    done = __all_sync(0xffffffffu, done);
+    if (!done && lane == 0) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (done && blockIdx.x == 0) {
+        for (int half = 0; half < 2; ++half) {
+            uint32_t r[32];
+            for (int q = 0; q < 2; ++q) {
+                const uint32_t a = taddr + ((uint32_t)(warp * 32) << 16) + half * 64 + q * 32;
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                             "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                             "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                               "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                               "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+                               "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+                               "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                             : "r"(a));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                for (int j = 0; j < 32; ++j) D[(warp * 32 + lane) * 128 + half * 64 + q * 32 + j] = __uint_as_float(r[j]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(taddr));
+}
+
 // each thread: `iters` rounds of 4 red.global.add.f32 at pseudo-random word addresses
 __global__ void __launch_bounds__(128) k_red(float *__restrict__ buf, uint32_t mask, int iters)
 {
@@ -244,6 +343,17 @@ int peaks_gather_lines(const float *buf, uint32_t mask, int group, int grid, int
     else if (group == 2) k_gather_lines<2><<<grid, 128, 0, st>>>(buf, mask, iters, out);
     else if (group == 4) k_gather_lines<4><<<grid, 128, 0, st>>>(buf, mask, iters, out);
     else return (int)cudaErrorInvalidValue;
+    return (int)cudaPeekAtLastError();
+}
+
+// tensor-core TF32 products: grid CTAs x iters x 2 x 128 x 128 x 32 FLOP; D (128 x 128) from CTA
+// 0; A, B: 128 x 32 row-major; err (one int, zeroed by the caller) set on a time-out
+int peaks_tc_tf32(const float *A, const float *B, float *D, int grid, int iters, int *err, void *stream)
+{
+    const int smem = 32768 + 1024 + 64;
+    cudaError_t e = cudaFuncSetAttribute(k_tc_tf32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return (int)e;
+    k_tc_tf32<<<grid, 128, smem, static_cast<cudaStream_t>(stream)>>>(A, B, D, iters, err);
     return (int)cudaPeekAtLastError();
 }
 

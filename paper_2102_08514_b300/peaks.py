@@ -15,6 +15,9 @@
 * ``gather_line{1,2,4}_gsectors_s`` -- the same 4-byte gathers with groups of 1, 2 or 4 lanes
   reading different sectors of one pseudo-random 128-byte line in every instruction: sectors per
   second when one L1 -> L2 request carries 1, 2 or 4 sectors;
+* ``tc_tf32_tflops`` -- tensor-core TF32 products by ``tcgen05.mma kind::tf32`` (one CTA per SM,
+  operands in shared memory, accumulator in TMEM); ``tc_tf32_product_exact`` -- one 128 x 128 x 32
+  product with TF32-exact inputs equals the host's;
 * ``red_gatomics_s`` -- red.global.add.f32 at pseudo-random addresses of an L2-resident buffer
   (the adjoint's scatter);
 * ``shared_atomic_{f32,u32,u64}_gops_s`` -- shared-memory atomic adds at pseudo-random elements:
@@ -48,9 +51,10 @@ def _lib():
         _LIB.peaks_gather.argtypes = [v, ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int, v, v]
         _LIB.peaks_gather_lines.argtypes = [v, ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int, v, v]
         _LIB.peaks_red.argtypes = [v, ctypes.c_uint32, ctypes.c_int, ctypes.c_int, v]
+        _LIB.peaks_tc_tf32.argtypes = [v, v, v, ctypes.c_int, ctypes.c_int, v, v]
         _LIB.peaks_shared_atomic.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, v, v]
         for f in (_LIB.peaks_fma, _LIB.peaks_l2_read, _LIB.peaks_gather, _LIB.peaks_gather_lines, _LIB.peaks_red,
-                  _LIB.peaks_shared_atomic):
+                  _LIB.peaks_shared_atomic, _LIB.peaks_tc_tf32):
             f.restype = ctypes.c_int
     return _LIB
 
@@ -144,6 +148,25 @@ def measure(torch=None) -> dict:
         ms = _best_ms(torch, lambda: _check(lib.peaks_shared_atomic(t, sgrid, siters, ctypes.c_void_p(sout.data_ptr()), st),
                                             "peaks_shared_atomic"))
         res[name] = sgrid * 256 * 8 * siters / (ms * 1e-3) / 1e9
+    # tensor cores (tcgen05.mma kind::tf32): one exact 128 x 128 x 32 product checked against the
+    # host (inputs that TF32 holds exactly), then the rate of accumulating products
+    g = torch.Generator().manual_seed(2102)
+    ta = (torch.randint(-4, 5, (128, 32), generator=g).float() / 4).cuda()
+    tb = (torch.randint(-4, 5, (128, 32), generator=g).float() / 4).cuda()
+    td = torch.full((128, 128), float("nan"), device="cuda")
+    terr = torch.zeros(1, dtype=torch.int32, device="cuda")
+    _check(lib.peaks_tc_tf32(ctypes.c_void_p(ta.data_ptr()), ctypes.c_void_p(tb.data_ptr()),
+                             ctypes.c_void_p(td.data_ptr()), 1, 1, ctypes.c_void_p(terr.data_ptr()), st),
+           "peaks_tc_tf32")
+    torch.cuda.synchronize()
+    ref = (ta.double() @ tb.double().T).float()
+    res["tc_tf32_product_exact"] = bool(int(terr.item()) == 0 and torch.equal(td, ref))
+    tgrid, titers = sms, 2048
+    ms = _best_ms(torch, lambda: _check(lib.peaks_tc_tf32(ctypes.c_void_p(ta.data_ptr()), ctypes.c_void_p(tb.data_ptr()),
+                                                          ctypes.c_void_p(td.data_ptr()), tgrid, titers,
+                                                          ctypes.c_void_p(terr.data_ptr()), st), "peaks_tc_tf32"))
+    res["tc_tf32_tflops"] = tgrid * titers * 2.0 * 128 * 128 * 32 / (ms * 1e-3) / 1e12
+    res["tc_tf32_timeouts"] = int(terr.item())
     torch.cuda.synchronize()
     return res
 

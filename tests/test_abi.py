@@ -83,6 +83,6 @@ def test_peaks_library_exports_its_microbenchmarks():
     import ctypes
     from paper_2102_08514_b300 import peaks
     plib = ctypes.CDLL(peaks.library_path())
-    for name in ("peaks_fma", "peaks_l2_read", "peaks_gather", "peaks_gather_lines", "peaks_red",
+    for name in ("peaks_fma", "peaks_l2_read", "peaks_gather", "peaks_gather_lines", "peaks_red", "peaks_tc_tf32",
                  "peaks_shared_atomic"):
         assert hasattr(plib, name), name
