@@ -668,7 +668,8 @@ def run_ours(args):
                          "l2_gbs": sectors * 32 * n / (kern_ms * 1e-3) / 1e9 if sectors else None,
                          "l2_frac": sectors * 32 * n / (kern_ms * 1e-3) / 1e9 / pk["l2_read_gbs"] if sectors else None}},
         "peaks": {k: pk[k] for k in ("sms", "fp32_tflops", "gather_gsectors_s", "gather4B_l1_gloads_s",
-                                     "red_gatomics_s", "shared_atomic_f32_gops_s", "l2_read_gbs", "clocks")},
+                                     "gather_line2_gsectors_s", "gather_line4_gsectors_s", "red_gatomics_s",
+                                     "shared_atomic_f32_gops_s", "l2_read_gbs", "tc_tf32_tflops", "clocks")},
         "forms": {k: {"evals_per_s": (RAY_EVALS[0] if k.startswith("rays") else n) / (v * 1e-3), "ms": v}
                   for k, v in form_ms.items()},
     }
